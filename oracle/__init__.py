@@ -1,0 +1,299 @@
+"""FP64 CPU oracle of the rounded-KLT image-compression path (arXiv 2111.14239).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The product package never
+imports this module, and this module never imports the product package; the two
+share no code.  ``build()`` compiles ``rklt_oracle.c`` with gcc (plain C, OpenMP
+over blocks in ``pipeline`` only).
+
+Every function follows a passage of the paper (cited per function in
+``rklt_oracle.c``).  Parity status per function:
+  klt_closed_form, klt_jacobi, round_alpha, normalisation, zigzag, int_stage,
+  forward, zonal, inverse, sse, psnr, pipeline        -- pinned (tests/test_oracle_*.py)
+  coding_gain, transform_efficiency                   -- pinned for K, That_1, That_4 and
+                                                         the DCT; That_2 / That_3 values of
+                                                         Table 2 are not reproduced
+                                                         (parity unpinned for those rows)
+  mse_to_klt, total_error_energy                      -- pinned (Table 2, RDCT reference)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rklt_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+OK, ERR_ARG, ERR_SINGULAR, ERR_NOCONV = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, -O2, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           _SRC, "-o", _LIB + ".tmp", "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    L = ctypes.c_long
+    sig = {
+        "orc_markov_autocorr": (None, [I, D, P]),
+        "orc_klt_closed_form": (I, [I, D, P, P]),
+        "orc_klt_jacobi": (I, [I, D, P, P]),
+        "orc_round_alpha": (I, [I, D, P, P, P]),
+        "orc_normalisation": (I, [I, P, P, P]),
+        "orc_that": (None, [I, P, P, P]),
+        "orc_invert": (I, [I, P, P]),
+        "orc_zigzag": (None, [I, P, P]),
+        "orc_int_stage": (I, [I, P, P, I, I, L, P]),
+        "orc_forward": (I, [I, P, P, I, I, L, P]),
+        "orc_zonal": (I, [I, P, L, I, P]),
+        "orc_inverse": (I, [I, P, P, I, I, I, P, L]),
+        "orc_sse": (D, [P, L, P, L, I, I]),
+        "orc_psnr": (D, [D, I, I]),
+        "orc_recon_u8": (None, [P, L, I, I, P, L]),
+        "orc_pipeline": (D, [I, P, P, I, I, L, I, P, P, I]),
+        "orc_max_threads": (I, []),
+        "orc_coding_gain": (I, [I, D, P, P]),
+        "orc_transform_efficiency": (None, [I, D, P, P]),
+        "orc_mse_to_klt": (None, [I, D, P, P, P]),
+        "orc_total_error_energy": (None, [I, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise ValueError(f"oracle {what} failed with status {rc}")
+
+
+# --------------------------------------------------------------------------
+# Setup-time math (Sec. 2, Sec. 3)
+# --------------------------------------------------------------------------
+
+def markov_autocorr(n: int, rho: float) -> np.ndarray:
+    R = np.zeros((n, n))
+    _load().orc_markov_autocorr(n, rho, _p(R))
+    return R
+
+
+def klt_closed_form(n: int, rho: float):
+    K = np.zeros((n, n)); lam = np.zeros(n)
+    _check(_load().orc_klt_closed_form(n, rho, _p(K), _p(lam)), "klt_closed_form")
+    return K, lam
+
+
+def klt_jacobi(n: int, rho: float):
+    K = np.zeros((n, n)); lam = np.zeros(n)
+    _check(_load().orc_klt_jacobi(n, rho, _p(K), _p(lam)), "klt_jacobi")
+    return K, lam
+
+
+def round_alpha(K: np.ndarray, alpha: float):
+    """(T int32, tie_margin, ok) with T = floor(alpha*K + 1/2)."""
+    n = K.shape[0]
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    T = np.zeros((n, n), np.int32)
+    m = np.zeros(1)
+    rc = _load().orc_round_alpha(n, alpha, _p(K), _p(T), _p(m))
+    return T, float(m[0]), rc == OK
+
+
+def normalisation(T: np.ndarray):
+    """(s, orthogonal): S = diag(s) from Eq. 1."""
+    n = T.shape[0]
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    s = np.zeros(n); o = np.zeros(1, np.int32)
+    _check(_load().orc_normalisation(n, _p(T), _p(s), _p(o)), "normalisation")
+    return s, bool(o[0])
+
+
+def that(T: np.ndarray, s: np.ndarray) -> np.ndarray:
+    n = T.shape[0]
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    M = np.zeros((n, n))
+    _load().orc_that(n, _p(T), _p(s), _p(M))
+    return M
+
+
+def invert(M: np.ndarray) -> np.ndarray:
+    n = M.shape[0]
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    Mi = np.zeros((n, n))
+    _check(_load().orc_invert(n, _p(M), _p(Mi)), "invert")
+    return Mi
+
+
+def zigzag(n: int):
+    r = np.zeros(n * n, np.int32); c = np.zeros(n * n, np.int32)
+    _load().orc_zigzag(n, _p(r), _p(c))
+    return r, c
+
+
+def default_alpha(n: int) -> float:
+    """Expansion factor: 2 for N = 8 (Sec. 3); 2*sqrt(N/8) for other N (the
+    reading that keeps the N = 8 scaling relative to the sqrt(2/N) amplitude)."""
+    return 2.0 * (n / 8.0) ** 0.5
+
+
+class Plan:
+    """T, s, That and friends for (N, rho, alpha), derived by the closed form."""
+
+    def __init__(self, n: int, rho: float, alpha: float | None = None, route: str = "closed"):
+        self.n, self.rho = n, rho
+        self.alpha = default_alpha(n) if alpha is None else alpha
+        K, lam = (klt_closed_form if route == "closed" else klt_jacobi)(n, rho)
+        self.K, self.lam = K, lam
+        T, margin, ok = round_alpha(K, self.alpha)
+        if not ok:
+            raise ValueError("rounded entries outside {0, +1, -1}")
+        self.T, self.tie_margin = T, margin
+        self.s, self.orthogonal = normalisation(T)
+        self.That = that(T, self.s)
+
+
+# --------------------------------------------------------------------------
+# Per-image path (Sec. 4.1, Appendix)
+# --------------------------------------------------------------------------
+
+def _img(img: np.ndarray):
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    return img, H, W
+
+
+def int_stage(n: int, T: np.ndarray, img: np.ndarray) -> np.ndarray:
+    """C = T A T^T per block, int64, shape (nblk, n, n)."""
+    img, H, W = _img(img)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    C = np.zeros(((H // n) * (W // n), n, n), np.int64)
+    _check(_load().orc_int_stage(n, _p(T), _p(img), H, W, W, _p(C)), "int_stage")
+    return C
+
+
+def forward(n: int, M: np.ndarray, img: np.ndarray) -> np.ndarray:
+    """B = M A M^T per block in zig-zag order, shape (nblk, n*n)."""
+    img, H, W = _img(img)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    B = np.zeros(((H // n) * (W // n), n * n))
+    _check(_load().orc_forward(n, _p(M), _p(img), H, W, W, _p(B)), "forward")
+    return B
+
+
+def zonal(n: int, coef: np.ndarray, r: int) -> np.ndarray:
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    nblk = coef.shape[0]
+    out = np.zeros((nblk, r))
+    _check(_load().orc_zonal(n, _p(coef), nblk, r, _p(out)), "zonal")
+    return out
+
+
+def inverse(n: int, M: np.ndarray, zcoef: np.ndarray, r: int, H: int, W: int) -> np.ndarray:
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    zcoef = np.ascontiguousarray(zcoef, dtype=np.float64)
+    rec = np.zeros((H, W))
+    _check(_load().orc_inverse(n, _p(M), _p(zcoef), r, H, W, _p(rec), W), "inverse")
+    return rec
+
+
+def sse(img: np.ndarray, recon: np.ndarray) -> float:
+    img, H, W = _img(img)
+    recon = np.ascontiguousarray(recon, dtype=np.float64)
+    return float(_load().orc_sse(_p(img), W, _p(recon), W, H, W))
+
+
+def psnr(sse_value: float, H: int, W: int) -> float:
+    return float(_load().orc_psnr(sse_value, H, W))
+
+
+def recon_u8(recon: np.ndarray) -> np.ndarray:
+    recon = np.ascontiguousarray(recon, dtype=np.float64)
+    H, W = recon.shape
+    out = np.zeros((H, W), np.uint8)
+    _load().orc_recon_u8(_p(recon), W, H, W, _p(out), W)
+    return out
+
+
+def pipeline(n: int, M: np.ndarray, img: np.ndarray, r: int, want_coef: bool = False,
+             want_recon: bool = False, nthreads: int = 0):
+    """Forward, zonal r, inverse and SSE in one pass.  Returns (sse, zcoef|None, recon|None)."""
+    img, H, W = _img(img)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    nblk = (H // n) * (W // n)
+    zc = np.zeros((nblk, r)) if want_coef else None
+    rc = np.zeros((H, W)) if want_recon else None
+    s = _load().orc_pipeline(n, _p(M), _p(img), H, W, W, r,
+                             _p(zc) if zc is not None else None,
+                             _p(rc) if rc is not None else None, nthreads)
+    if s < 0:
+        raise ValueError(f"oracle pipeline failed ({s})")
+    return float(s), zc, rc
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+# --------------------------------------------------------------------------
+# Figures of merit (Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def coding_gain(That: np.ndarray, rho: float) -> float:
+    n = That.shape[0]
+    M = np.ascontiguousarray(That, dtype=np.float64)
+    out = np.zeros(1)
+    _check(_load().orc_coding_gain(n, rho, _p(M), _p(out)), "coding_gain")
+    return float(out[0])
+
+
+def transform_efficiency(That: np.ndarray, rho: float) -> float:
+    n = That.shape[0]
+    M = np.ascontiguousarray(That, dtype=np.float64)
+    out = np.zeros(1)
+    _load().orc_transform_efficiency(n, rho, _p(M), _p(out))
+    return float(out[0])
+
+
+def mse_to_klt(K: np.ndarray, That: np.ndarray, rho: float) -> float:
+    n = K.shape[0]
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    M = np.ascontiguousarray(That, dtype=np.float64)
+    out = np.zeros(1)
+    _load().orc_mse_to_klt(n, rho, _p(K), _p(M), _p(out))
+    return float(out[0])
+
+
+def total_error_energy(K: np.ndarray, That: np.ndarray) -> float:
+    n = K.shape[0]
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    M = np.ascontiguousarray(That, dtype=np.float64)
+    out = np.zeros(1)
+    _load().orc_total_error_energy(n, _p(K), _p(M), _p(out))
+    return float(out[0])
