@@ -1,0 +1,202 @@
+/*
+ * rklt.h -- C ABI of the GB300 (sm_103a) rounded-KLT image-compression library.
+ *
+ * Method: "Low-complexity Rounded KLT Approximation for Image Compression"
+ * (Radunz, Bayer, Cintra; arXiv 2111.14239).  Per N x N block A of an 8-bit
+ * image the library computes the integer stage C = T A T^T (T = round(alpha K),
+ * K the KLT of a first-order Markov process with correlation rho, Sec. 2.1 and
+ * Sec. 2.3), the normalised coefficients B = S C S (S from Eq. 1, the Appendix's
+ * (u u^T) o (T A T^T) form), keeps the first r coefficients in zig-zag order
+ * (Sec. 4.1), reconstructs A' = That^{-1} B' That^{-T} (Sec. 4.1, Appendix), and
+ * reduces the squared error to MSE / PSNR with peak 255 (Sec. 4.1, Table 3).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns rklt_status; RKLT_OK (0) on success.  On failure
+ *    nothing has been enqueued, and rklt_last_error() (per host thread) holds a
+ *    one-line reason.  No C++ exception crosses this boundary.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device work is enqueued asynchronously on it; the call
+ *    returns before the GPU finishes.  Errors raised by a kernel while it runs
+ *    (a bounded wait that gave up) are latched on the device and reported by
+ *    rklt_device_status().
+ *  - Pointers named d_* are device pointers that the CALLER allocates and owns;
+ *    h_* are host pointers.  The library never frees caller memory.
+ *  - Images: uint8, row-major, H rows of W pixels, row pitch `ld` bytes (ld >= W).
+ *    H and W must be multiples of N (disjoint N x N blocks, Sec. 4.1), else
+ *    RKLT_ERR_SHAPE.  H = 0 or W = 0 is a valid empty image.
+ *  - Blocks are numbered row-major over the (H/N) x (W/N) block grid; batched
+ *    calls place image i's blocks after those of images 0..i-1.
+ *  - Zig-zag: coefficient (i, j) of a block (i = vertical frequency, j =
+ *    horizontal) has zig-zag index z(i, j); the walk visits anti-diagonals i + j
+ *    in order, moving down-left on odd ones and up-right on even ones, i.e. the
+ *    JPEG order for N = 8.
+ *  - Precision: the integer stage is exact (bit-identical to integer
+ *    arithmetic); normalisation, inverse and error are FP32 with FP64 per-tile
+ *    and per-image accumulation.  FP64 is used on the host only, to build plans.
+ */
+#ifndef RKLT_H
+#define RKLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int rklt_status;
+#define RKLT_OK 0
+#define RKLT_ERR_ARG 1         /* bad argument (N, rho, alpha, r, NULL pointer, count) */
+#define RKLT_ERR_SHAPE 2       /* H or W not a multiple of N, ld < W, bad strides    */
+#define RKLT_ERR_DEGENERATE 3  /* T has a zero row, is singular, has an entry outside
+                                  {0, +1, -1}, lacks the row parity of the KLT, or an
+                                  entry of alpha*K lies within 1e-9 of a rounding tie */
+#define RKLT_ERR_CUDA 4        /* a CUDA runtime call failed                          */
+#define RKLT_ERR_OOM 5         /* a library-owned device or host allocation failed    */
+#define RKLT_ERR_BUDGET 6      /* serving: request exceeds the device-memory budget   */
+#define RKLT_ERR_TIMEOUT 7     /* a bounded device-side wait gave up                  */
+#define RKLT_ERR_UNSUPPORTED 8 /* valid request this build does not handle            */
+
+/* Thread-local description of the last failure on this host thread. */
+const char *rklt_last_error(void);
+/* Static name of a status code. */
+const char *rklt_status_string(rklt_status s);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int rklt_version(void);
+
+/* ------------------------------------------------------------------------
+ * Plans (Sec. 2.1, Sec. 2.3, Eq. 1) -- built on the host in FP64, uploaded once.
+ * ------------------------------------------------------------------------ */
+
+typedef struct rklt_plan rklt_plan;
+
+/* Build the RKLT plan for block size N in {4, 8, 16, 32} and correlation
+ * 0 < rho < 1 with the default expansion factor alpha = 2 sqrt(N/8) (alpha = 2
+ * for N = 8, Sec. 3).  Steps: omega roots of the Sec. 2.1 equation by
+ * bisection, one per interval (i pi/N, (i+1) pi/N); K from the closed form
+ * (sign: K[i][0] > 0); T = floor(alpha K + 1/2) (Eq. 2); s_i = 1/sqrt((T T^T)_ii)
+ * (Eq. 1); T^{-1} in FP64; zig-zag table.  On success *out owns host tables and
+ * nothing on the device (plan tables travel as kernel parameters); release it
+ * with rklt_destroy.  Plans are immutable, so concurrent use from several host
+ * threads and streams is safe.
+ * Errors: RKLT_ERR_ARG (N, rho, out), RKLT_ERR_DEGENERATE, RKLT_ERR_OOM. */
+rklt_status rklt_make(int N, double rho, rklt_plan **out);
+
+/* As rklt_make with an explicit expansion factor alpha > 0 (Sec. 2.3). */
+rklt_status rklt_make_alpha(int N, double rho, double alpha, rklt_plan **out);
+
+/* Build a plan from a caller-supplied integer matrix T (h_T: N*N int8, row-major,
+ * entries in {0, +1, -1}, rows with the parity T[i][N-1-j] = (-1)^i T[i][j]).
+ * Used to run the paper's printed matrices (Table 1) directly.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_DEGENERATE, RKLT_ERR_OOM. */
+rklt_status rklt_make_from_matrix(int N, const int8_t *h_T, rklt_plan **out);
+
+/* Free a plan (NULL is ignored).  Work already enqueued with it is unaffected. */
+void rklt_destroy(rklt_plan *plan);
+
+/* Plan introspection into caller-owned host buffers; any output may be NULL.
+ * h_T: N*N int8 row-major; h_s: N doubles (diagonal of S); *orthogonal = 1 when
+ * T T^T is diagonal (Eq. 1, first branch); *N_out = N; *alpha_out, *rho_out as
+ * built (rho = 0 for rklt_make_from_matrix). */
+rklt_status rklt_plan_info(const rklt_plan *plan, int8_t *h_T, double *h_s, int *orthogonal,
+                           int *N_out, double *alpha_out, double *rho_out);
+
+/* ------------------------------------------------------------------------
+ * Split path (Sec. 4.1): forward -> zonal -> inverse -> psnr.
+ * ------------------------------------------------------------------------ */
+
+/* Exact integer stage C = T A T^T of every block, int32, raster order inside a
+ * block: d_C[blk][i][j] (N*N per block).  |C| <= (nnz per row)^2 * 255.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_forward_int(const rklt_plan *plan, const uint8_t *d_img, int H, int W,
+                             int64_t ld, int32_t *d_C, void *stream);
+
+/* Normalised forward transform B = That A That^T = (s s^T) o C of every block,
+ * FP32, zig-zag order: d_coef[blk][z] with z = 0..N*N-1.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_forward(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld,
+                         float *d_coef, void *stream);
+
+/* Zonal retention (Sec. 4.1): d_out[blk][k] = d_coef[blk][k] for k < r, i.e.
+ * the first r zig-zag coefficients of each of nblk blocks, compact.  0 <= r <= N*N.
+ * d_out may equal d_coef only when r == N*N.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_CUDA. */
+rklt_status rklt_zonal(const rklt_plan *plan, const float *d_coef, int64_t nblk, int r,
+                       float *d_out, void *stream);
+
+/* Inverse transform (Sec. 4.1, Appendix): from compact coefficients d_zcoef
+ * [blk][r] (zero beyond r), A' = That^{-1} B' That^{-T} per block into d_recon,
+ * FP32, H x W with row pitch ld_out floats (ld_out >= W).  Unrounded.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_inverse(const rklt_plan *plan, const float *d_zcoef, int r, int H, int W,
+                         float *d_recon, int64_t ld_out, void *stream);
+
+/* Squared error and PSNR (Sec. 4.1, Table 3): *d_sse = sum (A - A')^2 (FP64),
+ * *d_psnr = 10 log10(255^2 H W / SSE) (FP32; +inf when SSE = 0; NaN for an empty
+ * image).  Both scalars are device memory; reading them is the caller's job.
+ * ldr is the pitch of d_recon in floats.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_psnr(const uint8_t *d_img, int64_t ld, const float *d_recon, int64_t ldr,
+                      int H, int W, double *d_sse, float *d_psnr, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Fused single pass: forward + zonal + inverse + error, nothing in between
+ * touches HBM.
+ * ------------------------------------------------------------------------ */
+
+/* One image.  Outputs (each optional, NULL to skip except the scalars):
+ *   d_zcoef  [blk][r] FP32 compact zig-zag coefficients (as rklt_forward + rklt_zonal);
+ *   d_recon  uint8 reconstruction clip(floor(A' + 1/2), 0, 255), pitch ld_recon bytes;
+ *   d_sse    FP64 SSE of the unrounded reconstruction; d_psnr FP32 PSNR (as rklt_psnr).
+ * The reconstruction uses A' = T^{-1} (M o C) T^{-T}, which equals That^{-1} B' That^{-T}
+ * because the diagonal S cancels (Appendix).
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_fused(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld, int r,
+                       float *d_zcoef, uint8_t *d_recon, int64_t ld_recon, double *d_sse,
+                       float *d_psnr, void *stream);
+
+/* nimg images of one shape in one launch.  Image i starts at d_img + i*img_stride
+ * (bytes); its reconstruction at d_recon + i*recon_stride; its coefficients after
+ * those of images 0..i-1; d_sse[i], d_psnr[i] are its scalars.  When the base
+ * pointers and pitches are 16-byte aligned the tiles move by TMA (bulk tensor
+ * copies through a shared-memory ring); otherwise by vector loads.  Results are
+ * bit-identical either way and independent of nimg.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
+rklt_status rklt_fused_batched(const rklt_plan *plan, const uint8_t *d_img, int nimg, int H, int W,
+                               int64_t ld, int64_t img_stride, int r, float *d_zcoef,
+                               uint8_t *d_recon, int64_t ld_recon, int64_t recon_stride,
+                               double *d_sse, float *d_psnr, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Device status
+ * ------------------------------------------------------------------------ */
+
+/* Synchronises the current device, then returns and clears the library's latched
+ * device-side error: RKLT_OK, or RKLT_ERR_TIMEOUT when a bounded wait inside a
+ * kernel gave up (the kernel then skipped its remaining work and returned). */
+rklt_status rklt_device_status(void);
+
+/* Bound, in microseconds of GPU time (%globaltimer), on every device-side wait
+ * (TMA-ring mbarrier waits) of kernels launched after this call from this
+ * process; 0 restores the default of 4 seconds.  A wait that exceeds it latches
+ * RKLT_ERR_TIMEOUT (see rklt_device_status) and ends its kernel early. */
+void rklt_set_wait_timeout_us(uint32_t microseconds);
+
+/* Transport of the fused kernel's tiles for later calls from this process:
+ * 0 (default) = TMA bulk tensor copies when pointers and pitches are 16-byte
+ * aligned, else plain loads; 1 = plain loads always.  Results are identical;
+ * the switch exists so that both transports can be tested on the same data. */
+void rklt_set_transport(int mode);
+
+/* Fault injection for tests of the bounded waits: while on (non-zero), the TMA
+ * producer of later fused launches issues no tile loads, so the consumers' waits
+ * run out after the rklt_set_wait_timeout_us limit; the kernel then returns early
+ * without touching its outputs and rklt_device_status() reports RKLT_ERR_TIMEOUT.
+ * No memory access is skipped or misdirected; nothing faults. */
+void rklt_debug_inject_stall(int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKLT_H */

@@ -1,0 +1,242 @@
+"""Python binding of the GB300 rounded-KLT library (librklt.so, C ABI in include/rklt.h).
+
+Argument marshalling only: every step of the transform runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU fallback:
+if the library cannot be built or loaded, importing this package raises.
+
+Names follow the C ABI: rklt_make, rklt_forward, rklt_zonal, rklt_inverse,
+rklt_psnr, rklt_fused, rklt_fused_batched, ...  Functions take torch tensors
+(device tensors for d_* arguments) and an optional torch.cuda.Stream (default:
+the current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import _build
+
+__all__ = [
+    "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
+    "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
+    "rklt_fused", "rklt_fused_batched", "rklt_device_status", "rklt_set_wait_timeout_us",
+    "rklt_set_transport", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
+]
+
+STATUS = {0: "RKLT_OK", 1: "RKLT_ERR_ARG", 2: "RKLT_ERR_SHAPE", 3: "RKLT_ERR_DEGENERATE", 4: "RKLT_ERR_CUDA",
+          5: "RKLT_ERR_OOM", 6: "RKLT_ERR_BUDGET", 7: "RKLT_ERR_TIMEOUT", 8: "RKLT_ERR_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "rklt.h")
+
+
+class RklTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.build()
+    return ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
+lib = _load()
+
+_P, _I, _D, _L, _U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint32
+_SIGS = {
+    "rklt_last_error": (ctypes.c_char_p, []),
+    "rklt_status_string": (ctypes.c_char_p, [_I]),
+    "rklt_version": (_I, []),
+    "rklt_make": (_I, [_I, _D, ctypes.POINTER(_P)]),
+    "rklt_make_alpha": (_I, [_I, _D, _D, ctypes.POINTER(_P)]),
+    "rklt_make_from_matrix": (_I, [_I, _P, ctypes.POINTER(_P)]),
+    "rklt_destroy": (None, [_P]),
+    "rklt_plan_info": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "rklt_forward_int": (_I, [_P, _P, _I, _I, _L, _P, _P]),
+    "rklt_forward": (_I, [_P, _P, _I, _I, _L, _P, _P]),
+    "rklt_zonal": (_I, [_P, _P, _L, _I, _P, _P]),
+    "rklt_inverse": (_I, [_P, _P, _I, _I, _I, _P, _L, _P]),
+    "rklt_psnr": (_I, [_P, _L, _P, _L, _I, _I, _P, _P, _P]),
+    "rklt_fused": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
+    "rklt_fused_batched": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P]),
+    "rklt_device_status": (_I, []),
+    "rklt_set_wait_timeout_us": (None, [_U32]),
+    "rklt_set_transport": (None, [_I]),
+    "rklt_debug_inject_stall": (None, [_I]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def header_symbols() -> list:
+    """Function names declared in include/rklt.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rklt_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != 0:
+        raise RklTError(status, lib.rklt_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_alpha(n: int) -> float:
+    return 2.0 * (n / 8.0) ** 0.5
+
+
+def nblocks(n: int, h: int, w: int) -> int:
+    return (h // n) * (w // n)
+
+
+class Plan:
+    """Owns an rklt_plan handle (host tables; the library frees it on close)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        n = ctypes.c_int()
+        a = ctypes.c_double()
+        rho = ctypes.c_double()
+        o = ctypes.c_int()
+        _check(lib.rklt_plan_info(self._h, None, None, ctypes.byref(o), ctypes.byref(n), ctypes.byref(a),
+                                  ctypes.byref(rho)))
+        self.N, self.alpha, self.rho, self.orthogonal = n.value, a.value, rho.value, bool(o.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        """(T int8 numpy [N,N], s float64 numpy [N], orthogonal)."""
+        import numpy as np
+        T = np.zeros((self.N, self.N), np.int8)
+        s = np.zeros(self.N, np.float64)
+        o = ctypes.c_int()
+        _check(lib.rklt_plan_info(self._h, T.ctypes.data, s.ctypes.data, ctypes.byref(o), None, None, None))
+        return T, s, bool(o.value)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.rklt_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rklt_make(n: int, rho: float) -> Plan:
+    h = ctypes.c_void_p()
+    _check(lib.rklt_make(n, rho, ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def rklt_make_alpha(n: int, rho: float, alpha: float) -> Plan:
+    h = ctypes.c_void_p()
+    _check(lib.rklt_make_alpha(n, rho, alpha, ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def rklt_make_from_matrix(n: int, T) -> Plan:
+    import numpy as np
+    T = np.ascontiguousarray(T, dtype=np.int8)
+    h = ctypes.c_void_p()
+    _check(lib.rklt_make_from_matrix(n, T.ctypes.data, ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def rklt_plan_info(plan: Plan):
+    return plan.info()
+
+
+def _img_args(img):
+    """(ptr, H, W, ld) of a 2-D uint8 tensor with unit column stride."""
+    assert img.dim() == 2 and img.stride(1) == 1, "image must be 2-D with contiguous rows"
+    return img.data_ptr(), img.shape[0], img.shape[1], img.stride(0)
+
+
+def rklt_forward_int(plan: Plan, img, C, stream=None):
+    p, H, W, ld = _img_args(img)
+    _check(lib.rklt_forward_int(plan.handle, p, H, W, ld, _ptr(C), _stream(stream)))
+
+
+def rklt_forward(plan: Plan, img, coef, stream=None):
+    p, H, W, ld = _img_args(img)
+    _check(lib.rklt_forward(plan.handle, p, H, W, ld, _ptr(coef), _stream(stream)))
+
+
+def rklt_zonal(plan: Plan, coef, nblk: int, r: int, out, stream=None):
+    _check(lib.rklt_zonal(plan.handle, _ptr(coef), nblk, r, _ptr(out), _stream(stream)))
+
+
+def rklt_inverse(plan: Plan, zcoef, r: int, H: int, W: int, recon, stream=None):
+    ld = recon.stride(0) if recon is not None and hasattr(recon, "stride") else W
+    _check(lib.rklt_inverse(plan.handle, _ptr(zcoef), r, H, W, _ptr(recon), ld, _stream(stream)))
+
+
+def rklt_psnr(img, recon, sse, psnr, stream=None):
+    p, H, W, ld = _img_args(img)
+    _check(lib.rklt_psnr(p, ld, _ptr(recon), recon.stride(0), H, W, _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+def rklt_fused(plan: Plan, img, r: int, sse, psnr, zcoef=None, recon=None, stream=None):
+    p, H, W, ld = _img_args(img)
+    ldr = recon.stride(0) if recon is not None else 0
+    _check(lib.rklt_fused(plan.handle, p, H, W, ld, r, _ptr(zcoef), _ptr(recon), ldr, _ptr(sse), _ptr(psnr),
+                          _stream(stream)))
+
+
+def rklt_fused_batched(plan: Plan, imgs, r: int, sse, psnr, zcoef=None, recon=None, stream=None):
+    """imgs: uint8 tensor [nimg, H, W] (rows contiguous); recon likewise or None."""
+    assert imgs.dim() == 3 and imgs.stride(2) == 1
+    nimg, H, W = imgs.shape
+    ld, istr = imgs.stride(1), imgs.stride(0)
+    if recon is not None:
+        ldr, rstr = recon.stride(1), recon.stride(0)
+    else:
+        ldr, rstr = 0, 0
+    _check(lib.rklt_fused_batched(plan.handle, imgs.data_ptr(), nimg, H, W, ld, istr, r, _ptr(zcoef), _ptr(recon),
+                                  ldr, rstr, _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+def rklt_device_status():
+    _check(lib.rklt_device_status())
+
+
+def rklt_set_wait_timeout_us(us: int):
+    lib.rklt_set_wait_timeout_us(us)
+
+
+def rklt_set_transport(mode: int):
+    lib.rklt_set_transport(mode)
+
+
+def rklt_debug_inject_stall(on: bool):
+    lib.rklt_debug_inject_stall(1 if on else 0)
+
+
+def rklt_version() -> int:
+    return lib.rklt_version()

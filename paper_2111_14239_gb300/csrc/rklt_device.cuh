@@ -1,0 +1,173 @@
+// rklt_device.cuh -- device helpers shared by the library's kernels: TMA and
+// mbarrier PTX wrappers, bounded waits, the zig-zag walk, the latched device
+// error word, and byte/float conversions.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace rklt {
+
+// Latched device-side status (RKLT_OK or RKLT_ERR_TIMEOUT).  Without relocatable
+// device code every translation unit has its own copy; each unit exports a host
+// function that reads and clears it.
+static __device__ unsigned int g_dev_status = 0;
+
+// --------------------------------------------------------------------------
+// Zig-zag walk over an N x N coefficient block (Sec. 4.1, "standard zig-zag"):
+// anti-diagonals d = i + j in increasing order, odd d walked with the row
+// increasing, even d with the row decreasing; JPEG order for N = 8.  For even N
+// the walk is point-symmetric: position N*N-1-k mirrors position k.
+// --------------------------------------------------------------------------
+__host__ __device__ constexpr int zz_index(int N, int i, int j) {
+    int d = i + j;
+    if (d < N) return d * (d + 1) / 2 + ((d & 1) ? i : d - i);
+    int m = 2 * N - 2 - d;
+    int base = N * N - (m + 1) * (m + 2) / 2;
+    return base + ((d & 1) ? i - (d - (N - 1)) : (N - 1 - i));
+}
+
+__host__ __device__ constexpr int zz_upper_diag(int k) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= k) d++;
+    return d;
+}
+
+__host__ __device__ constexpr int zz_row(int N, int k) {
+    if (k < N * (N + 1) / 2) {
+        int d = zz_upper_diag(k), off = k - d * (d + 1) / 2;
+        return (d & 1) ? off : d - off;
+    }
+    int kk = N * N - 1 - k;
+    int d = zz_upper_diag(kk), off = kk - d * (d + 1) / 2;
+    return N - 1 - ((d & 1) ? off : d - off);
+}
+
+__host__ __device__ constexpr int zz_col(int N, int k) {
+    if (k < N * (N + 1) / 2) {
+        int d = zz_upper_diag(k), off = k - d * (d + 1) / 2;
+        return d - ((d & 1) ? off : d - off);
+    }
+    int kk = N * N - 1 - k;
+    int d = zz_upper_diag(kk), off = kk - d * (d + 1) / 2;
+    return N - 1 - (d - ((d & 1) ? off : d - off));
+}
+
+// --------------------------------------------------------------------------
+// PTX wrappers (sm_90+ forms that sm_103a keeps)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after timeout_ns of GPU
+// time; on give-up the device status latches RKLT_ERR_TIMEOUT (7).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > timeout_ns) {
+            atomicExch(&g_dev_status, 7u);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 3-D tiled bulk tensor load global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 3-D tiled bulk tensor store shared -> global (out-of-range elements are dropped).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z, const void *smem_src) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group"
+        " [%0, {%1, %2, %3}], [%4];" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Barrier over the first `count` threads of the CTA that also ORs a predicate.
+__device__ __forceinline__ bool named_any(int id, int count, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(pred)), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+// Barrier over the first `count` threads of the CTA (named barrier `id`).
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// --------------------------------------------------------------------------
+// Numeric helpers
+// --------------------------------------------------------------------------
+// Byte k of a 32-bit word as an exact float.
+__device__ __forceinline__ float byte_f(uint32_t w, int k) { return float((w >> (8 * k)) & 0xffu); }
+
+// clip(floor(x + 1/2), 0, 255): round-half-up then saturate to 8 bits.
+__device__ __forceinline__ uint32_t recon_byte(float x) {
+    float v = fminf(fmaxf(x + 0.5f, 0.0f), 255.0f);
+    return __float2uint_rd(v);
+}
+
+}  // namespace rklt

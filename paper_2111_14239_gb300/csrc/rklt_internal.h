@@ -1,0 +1,110 @@
+// rklt_internal.h -- declarations shared by the library's translation units.
+// Not installed; the public boundary is include/rklt.h.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rklt.h"
+
+namespace rklt {
+
+// Per-plan tables passed to kernels by value (they land in the constant bank,
+// so the transform loops read T and T^{-1} as immediate-style operands).
+//
+// Parity of the KLT rows (R is centrosymmetric): T[i][N-1-j] = (-1)^i T[i][j],
+// hence T^{-1}[N-1-l][j] = (-1)^j T^{-1}[l][j].  Only half of each matrix is
+// stored; the kernels' butterflies rebuild the rest.
+template <int N>
+struct PlanK {
+    float T[N][N / 2];    // T[i][j], j < N/2           (entries 0, +1, -1)
+    float Ti[N / 2][N];   // T^{-1}[l][j], l < N/2      (inverse of the bare integer T)
+    float Tih[N / 2][N];  // That^{-1}[l][j] = T^{-1}[l][j] / s_j
+    float sij[N][N];      // s_i * s_j (B = sij o C), rounded once from FP64
+    float s[N];           // s_i
+};
+
+// Host-side plan object behind the opaque rklt_plan handle.
+struct Plan {
+    int N = 0;
+    double rho = 0.0, alpha = 0.0;
+    int orthogonal = 0;
+    std::vector<int8_t> T;       // N*N
+    std::vector<double> s;       // N
+    std::vector<double> Tinv;    // N*N, FP64 inverse of T
+    std::vector<unsigned char> k; // bytes of PlanK<N>
+    template <int M>
+    const PlanK<M> &kparams() const { return *reinterpret_cast<const PlanK<M> *>(k.data()); }
+};
+
+// Geometry and outputs of one fused launch (kernel parameter).
+struct FusedGeom {
+    const uint8_t *img;          // source (plain-load mode)
+    uint8_t *recon;              // 8-bit reconstruction (may be null)
+    float *zcoef;                // compact coefficients (may be null)
+    float *partials;             // one FP32 SSE partial per tile
+    int64_t ld, img_stride;      // source pitch / image stride (bytes)
+    int64_t ld_recon, recon_stride;
+    int64_t ntiles;              // nimg * tiles_y * tiles_x
+    int64_t blocks_per_img;      // (H/N) * (W/N)
+    int H, W, nimg;
+    int tiles_x, tiles_y;
+    int r, D;                    // retained coefficients, diagonal bound
+    int coef_vec4;               // r % 4 == 0 and zcoef 16-byte aligned
+    int use_tma;                 // tiles move by TMA (else plain loads)
+    int inject_stall;            // test hook: the producer issues no loads
+    uint64_t timeout_ns;
+};
+
+// Validated arguments of a fused call.
+struct FusedArgs {
+    const uint8_t *img;
+    int nimg, H, W;
+    int64_t ld, img_stride;
+    int r;
+    float *zcoef;
+    uint8_t *recon;
+    int64_t ld_recon, recon_stride;
+    double *sse;
+    float *psnr;
+    float *partials;   // caller-provided per-tile scratch, or null (library pool)
+    int force_plain;   // 1: plain loads even when TMA would apply
+};
+
+rklt_status launch_fused_n4(const Plan &p, const FusedArgs &a, cudaStream_t st);
+rklt_status launch_fused_n8(const Plan &p, const FusedArgs &a, cudaStream_t st);
+rklt_status launch_fused_n16(const Plan &p, const FusedArgs &a, cudaStream_t st);
+rklt_status launch_fused_n32(const Plan &p, const FusedArgs &a, cudaStream_t st);
+unsigned int take_status_n4();
+unsigned int take_status_n8();
+unsigned int take_status_n16();
+unsigned int take_status_n32();
+unsigned int take_status_split();
+
+// host helpers (rklt_host.cpp)
+rklt_status fail(rklt_status st, const std::string &msg);
+rklt_status cuda_fail(cudaError_t err, const char *what);
+cudaMemPool_t scratch_pool();                 // per-device stream-ordered pool for library scratch
+int sm_count(int dev);
+int ensure_smem_attr(const void *kernel);     // opt in to 227 KB dynamic smem; returns the device
+bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64_t ld, int64_t stride,
+                 int box_w, int box_h);
+int transport_mode();                         // 0 auto, 1 plain loads only
+int inject_stall();                           // fault-injection hook for the bounded-wait test
+
+// Largest zig-zag diagonal touched by the first r coefficients, plus one:
+// every retained (i, j) has i + j < diag_bound(N, r).
+int diag_bound(int N, int r);
+
+// Device wait timeout (nanoseconds) for the next launches.
+uint64_t wait_timeout_ns();
+
+}  // namespace rklt
+
+struct rklt_plan {
+    rklt::Plan p;
+};

@@ -1,0 +1,76 @@
+"""Host-side tests of the C-ABI library (no GPU needed): it loads, exports every
+entry point declared in include/rklt.h, and builds plans (host FP64) identical
+to the oracle's; bad arguments return the documented status codes."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import golden_io
+
+rk = pytest.importorskip("paper_2111_14239_gb300")
+
+RHOS = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.95, 0.99]
+
+
+def test_exports_every_header_symbol():
+    names = rk.header_symbols()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(rk.lib, name), name
+        getattr(rk.lib, name)  # resolves through dlsym
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
+def test_plans_match_oracle(orc, n):
+    for rho in RHOS:
+        plan = rk.rklt_make(n, rho)
+        T, s, orth = plan.info()
+        ref = orc.Plan(n, rho)
+        assert np.array_equal(T.astype(np.int32), ref.T), (n, rho)
+        assert np.max(np.abs(s - ref.s)) < 1e-15
+        assert orth == ref.orthogonal
+        assert plan.N == n and plan.alpha == pytest.approx(rk.default_alpha(n))
+
+
+def test_plans_reproduce_table1():
+    t1 = golden_io.table1()
+    for rho, name in ((0.2, "T1"), (0.5, "T2"), (0.7, "T3"), (0.85, "T4")):
+        T, s, _ = rk.rklt_make(8, rho).info()
+        assert np.array_equal(T.astype(np.int64), t1[name]["T"])
+        assert np.allclose(s, t1[name]["s"], atol=1e-15, rtol=0)
+        T2, s2, _ = rk.rklt_make_from_matrix(8, t1[name]["T"]).info()
+        assert np.array_equal(T2, T) and np.array_equal(s2, s)
+
+
+def test_status_codes():
+    h = ctypes.c_void_p()
+    assert rk.lib.rklt_make(5, 0.5, ctypes.byref(h)) == 1
+    assert rk.lib.rklt_make(8, 0.0, ctypes.byref(h)) == 1
+    assert rk.lib.rklt_make(8, 1.0, ctypes.byref(h)) == 1
+    assert rk.lib.rklt_make(8, 0.5, None) == 1
+    # alpha past 3/(2 gamma) rounds some entry to 2
+    assert rk.lib.rklt_make_alpha(8, 0.5, 4.0, ctypes.byref(h)) == 3
+    assert b"outside" in rk.lib.rklt_last_error()
+    # alpha = 2 at N = 32 rounds everything to zero
+    assert rk.lib.rklt_make_alpha(32, 0.95, 2.0, ctypes.byref(h)) == 3
+    # a matrix without the KLT row parity
+    bad = np.eye(8, dtype=np.int8)
+    assert rk.lib.rklt_make_from_matrix(8, bad.ctypes.data, ctypes.byref(h)) == 3
+    # singular: repeated row
+    T = golden_io.table1()["T4"]["T"].astype(np.int8).copy()
+    T[2] = T[0]
+    assert rk.lib.rklt_make_from_matrix(8, T.ctypes.data, ctypes.byref(h)) == 3
+    assert rk.lib.rklt_status_string(7) == b"RKLT_ERR_TIMEOUT"
+
+
+def test_argument_checks_without_gpu():
+    """Shape and argument errors are caught on the host before any launch."""
+    plan = rk.rklt_make(8, 0.95)
+    d = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert rk.lib.rklt_fused(plan.handle, d, 12, 16, 16, 10, None, None, 0, d, d, None) == 2   # H % 8
+    assert rk.lib.rklt_fused(plan.handle, d, 16, 16, 8, 10, None, None, 0, d, d, None) == 2    # ld < W
+    assert rk.lib.rklt_fused(plan.handle, d, 16, 16, 16, 65, None, None, 0, d, d, None) == 1   # r > 64
+    assert rk.lib.rklt_fused(plan.handle, d, 16, 16, 16, 10, None, None, 0, None, d, None) == 1
+    assert rk.lib.rklt_zonal(plan.handle, d, 4, 10, d, None) == 1                           # aliasing, r < 64
+    assert rk.lib.rklt_fused_batched(plan.handle, d, 2, 16, 16, 16, 100, 10, None, None, 0, 0, d, d, None) == 2
