@@ -162,6 +162,8 @@ def run_ours(args):
     import numpy as np
     import torch
 
+    global NS
+    NS = tuple(int(x) for x in args.block_sizes.split(","))
     import paper_2111_14239_gb300 as rk
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -244,10 +246,10 @@ def run_ours(args):
             pin_out[n]["rec"].copy_(outs[n]["rec"], non_blocking=True)
             pin_out[n]["ps"].copy_(outs[n]["ps"], non_blocking=True)
 
-    for _ in range(2):
+    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 10))
+    for _ in range(2 if e2e_steps else 0):
         e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_steps = max(2, min(args.steps, 10))
     if dist:
         dist.barrier()
     s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -263,7 +265,7 @@ def run_ours(args):
         e2e_ms = float(t.item())
     h2d = imgs_np.nbytes
     d2h = sum(pin_out[n]["zc"].numel() * 4 + pin_out[n]["rec"].numel() + NIMG * 4 for n in NS)
-    e2e_val = px_step * e2e_steps * world / (e2e_ms / 1e3) / 1e6
+    e2e_val = px_step * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
 
     psnr = {n: [round(float(x), 4) for x in outs[n]["ps"].cpu().tolist()[:2]] for n in NS}
 
@@ -321,6 +323,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--block-sizes", default="4,8,16,32", help="subset of N (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -133,8 +133,9 @@ def test_split_path(rk, orc, n, rho):
         ps = torch.zeros(1, dtype=torch.float32, device="cuda")
         rk.rklt_psnr(dev(img), rec, sse, ps)
         # the PSNR kernel itself is FP64: against the oracle's SSE of the same FP32 image
+        # (only the summation order differs)
         ref_same = orc.sse(img, rec.cpu().numpy().astype(np.float64))
-        assert sse.item() == pytest.approx(ref_same, rel=1e-12, abs=1e-9)
+        assert sse.item() == pytest.approx(ref_same, rel=1e-10, abs=1e-9)
         check_sse(sse.item(), orc.sse(img, rec_ref), H, W, n)
 
 
