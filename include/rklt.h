@@ -167,6 +167,34 @@ rklt_status rklt_fused_batched(const rklt_plan *plan, const uint8_t *d_img, int 
                                uint8_t *d_recon, int64_t ld_recon, int64_t recon_stride,
                                double *d_sse, float *d_psnr, void *stream);
 
+/* rklt_fused for callers that must not allocate.  (Not part of the paper: this
+ * is a deployment variant of the fused pass, with no counterpart in the method.)
+ *
+ * rklt_fused obtains a small per-call scratch buffer (one float per 64 x 256
+ * tile) from a stream-ordered memory pool.  Some callers cannot allow that: code
+ * running on a real-time path where an allocation may block or synchronise the
+ * device, plugins whose host framework owns the whole device-memory budget and
+ * leaves no room for a private pool, and callers that must keep every device
+ * allocation under their own bookkeeping.  This entry point allocates nothing: no
+ * cudaMalloc, cudaFree, pool or library allocation.  Its scratch is one fixed
+ * array of 65536 floats (256 KB) inside the library's device image, which every
+ * GPU that loads the library keeps until the process exits.
+ *
+ * Arguments, outputs and results are those of rklt_fused (bit-identical).
+ * Limit: the image may span at most 65536 tiles of 64 x 256 pixels
+ * (ceil(H/64) * ceil(W/256) <= 65536, e.g. 32768 x 32768); larger images are
+ * rejected with RKLT_ERR_ARG before anything is enqueued.
+ * Set-up: the first call on each device, made with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Sharing: all calls use the same array and each call
+ * overwrites it (no state carries over), so calls that may overlap on the GPU --
+ * on different streams, or from several host threads -- race and must be
+ * serialised by the caller.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA, RKLT_ERR_UNSUPPORTED. */
+rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld, int r,
+                               float *d_zcoef, uint8_t *d_recon, int64_t ld_recon, double *d_sse,
+                               float *d_psnr, void *stream);
+
 /* ------------------------------------------------------------------------
  * Device status
  * ------------------------------------------------------------------------ */

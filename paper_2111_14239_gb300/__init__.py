@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
     "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
-    "rklt_fused", "rklt_fused_batched", "rklt_device_status", "rklt_set_wait_timeout_us",
+    "rklt_fused", "rklt_fused_batched", "rklt_fused_noalloc", "rklt_device_status", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
 ]
 
@@ -61,6 +61,7 @@ _SIGS = {
     "rklt_psnr": (_I, [_P, _L, _P, _L, _I, _I, _P, _P, _P]),
     "rklt_fused": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_fused_batched": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P]),
+    "rklt_fused_noalloc": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_device_status": (_I, []),
     "rklt_set_wait_timeout_us": (None, [_U32]),
     "rklt_set_transport": (None, [_I]),
@@ -207,6 +208,14 @@ def rklt_fused(plan: Plan, img, r: int, sse, psnr, zcoef=None, recon=None, strea
     ldr = recon.stride(0) if recon is not None else 0
     _check(lib.rklt_fused(plan.handle, p, H, W, ld, r, _ptr(zcoef), _ptr(recon), ldr, _ptr(sse), _ptr(psnr),
                           _stream(stream)))
+
+
+def rklt_fused_noalloc(plan: Plan, img, r: int, sse, psnr, zcoef=None, recon=None, stream=None):
+    """rklt_fused without any allocation (scratch in the library's fixed device array)."""
+    p, H, W, ld = _img_args(img)
+    ldr = recon.stride(0) if recon is not None else 0
+    _check(lib.rklt_fused_noalloc(plan.handle, p, H, W, ld, r, _ptr(zcoef), _ptr(recon), ldr, _ptr(sse),
+                                  _ptr(psnr), _stream(stream)))
 
 
 def rklt_fused_batched(plan: Plan, imgs, r: int, sse, psnr, zcoef=None, recon=None, stream=None):

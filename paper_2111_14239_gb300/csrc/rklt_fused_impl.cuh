@@ -45,6 +45,7 @@ constexpr int TILE_BYTES = TW * TH;
 constexpr int STAGES = 4;        // TMA ring depth
 constexpr int NCONS = 256;       // consumer threads (8 warps); one producer warp follows
 constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchange buffer (floats)
+static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
 constexpr int REG_DMAX8 = 5;     // N = 8: register path up to this diagonal bound
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
 

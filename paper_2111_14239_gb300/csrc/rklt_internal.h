@@ -13,6 +13,10 @@
 
 namespace rklt {
 
+// Tile geometry of the fused kernel: 64 rows x 256 bytes per tile.
+constexpr int kTileW = 256;
+constexpr int kTileH = 64;
+
 // Per-plan tables passed to kernels by value (they land in the constant bank,
 // so the transform loops read T and T^{-1} as immediate-style operands).
 //

@@ -1,0 +1,89 @@
+// rklt_noalloc.cu -- rklt_fused without any allocation.
+//
+// rklt_fused takes its per-tile SSE partials (one float per 64 x 256 tile) from
+// a stream-ordered memory pool.  This variant takes them from a fixed array in
+// the library's own device memory instead, so a call performs no allocation of
+// any kind.  The array is a file-scope __device__ object: every GPU that loads
+// the library holds it (256 KB) until the process exits.  Host code cannot pass
+// the array's name to a kernel -- on the host that name denotes a stand-in
+// object, not device memory -- so its device address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+#include <mutex>
+
+#include "rklt_internal.h"
+
+namespace rklt {
+
+constexpr int64_t kNoAllocMaxTiles = 65536;  // 2^16 tiles of 64 x 256 pixels = 2^30 pixels
+
+static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxTiles];
+
+namespace {
+
+std::mutex g_mu;
+float *g_addr[64] = {};
+
+// Device address of g_noalloc_partials on the current device (first call per
+// device performs the lookup).
+rklt_status partials_address(float **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(RKLT_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch array");
+        g_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_addr[dev];
+    return RKLT_OK;
+}
+
+}  // namespace
+}  // namespace rklt
+
+using namespace rklt;
+
+extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld,
+                                          int r, float *d_zcoef, uint8_t *d_recon, int64_t ld_recon,
+                                          double *d_sse, float *d_psnr, void *stream) {
+    if (!plan) return fail(RKLT_ERR_ARG, "plan is NULL");
+    const int N = plan->p.N;
+    if (!d_sse || !d_psnr) return fail(RKLT_ERR_ARG, "d_sse and d_psnr are required");
+    if (r < 0 || r > N * N) return fail(RKLT_ERR_ARG, "r must lie in [0, N*N]");
+    if (H < 0 || W < 0 || H % N || W % N) return fail(RKLT_ERR_SHAPE, "H and W must be non-negative multiples of N");
+    if (ld < W) return fail(RKLT_ERR_SHAPE, "ld must be >= W");
+    if (H > 0 && W > 0 && !d_img) return fail(RKLT_ERR_ARG, "d_img is NULL");
+    if (d_recon && ld_recon < W) return fail(RKLT_ERR_SHAPE, "ld_recon must be >= W");
+    const int64_t tiles = int64_t((H + kTileH - 1) / kTileH) * ((W + kTileW - 1) / kTileW);
+    if (tiles > kNoAllocMaxTiles)
+        return fail(RKLT_ERR_ARG, "image too large for rklt_fused_noalloc: it needs " + std::to_string(tiles) +
+                                      " tiles of 64 x 256 pixels and the fixed scratch array holds 65536");
+    float *partials = nullptr;
+    rklt_status st = partials_address(&partials);
+    if (st != RKLT_OK) return st;
+    FusedArgs a{};
+    a.img = d_img;
+    a.nimg = 1;
+    a.H = H;
+    a.W = W;
+    a.ld = ld;
+    a.r = r;
+    a.zcoef = d_zcoef;
+    a.recon = d_recon;
+    a.ld_recon = ld_recon;
+    a.sse = d_sse;
+    a.psnr = d_psnr;
+    a.partials = partials;
+    a.force_plain = transport_mode() == 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (N) {
+        case 4: return launch_fused_n4(plan->p, a, s);
+        case 8: return launch_fused_n8(plan->p, a, s);
+        case 16: return launch_fused_n16(plan->p, a, s);
+        case 32: return launch_fused_n32(plan->p, a, s);
+        default: return fail(RKLT_ERR_ARG, "bad plan");
+    }
+}

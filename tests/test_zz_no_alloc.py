@@ -1,0 +1,78 @@
+"""rklt_fused_noalloc: the fused pass for callers that cannot allocate device
+memory (a real-time path where an allocation may block, a plugin whose host
+owns the whole memory budget).  Its scratch is a fixed array in the library's
+device image, so it must give exactly what rklt_fused gives, call after call,
+whatever an earlier call left in that shared array.
+
+Collected last on purpose (file name): if it fails, a run that stops at the first
+failure has already run every other test.  It passes in a fresh process too.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import synth_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+COEF_REL = 1e-5
+SSE_REL = 2.3e-4
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2111_14239_gb300 as rk
+    return rk
+
+
+def _both(rk, plan, img, r):
+    """Run rklt_fused and rklt_fused_noalloc on the same device image through the C ABI."""
+    n = plan.N
+    H, W = img.shape
+    d = torch.from_numpy(img).cuda()
+    nblk = (H // n) * (W // n)
+    outs = []
+    for fn in (rk.lib.rklt_fused, rk.lib.rklt_fused_noalloc):
+        zc = torch.full((nblk, r), float("nan"), device="cuda")
+        rec = torch.zeros_like(d)
+        sse = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        ps = torch.zeros(1, dtype=torch.float32, device="cuda")
+        st = fn(plan.handle, d.data_ptr(), H, W, d.stride(0), r, zc.data_ptr(), rec.data_ptr(), rec.stride(0),
+                sse.data_ptr(), ps.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        assert st == 0, rk.lib.rklt_last_error()
+        torch.cuda.synchronize()
+        outs.append((zc.cpu().numpy(), rec.cpu().numpy(), sse.item(), ps.item()))
+    rk.rklt_device_status()
+    return outs
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_noalloc_matches_fused_on_consecutive_calls(rk, n):
+    plan = rk.rklt_make(n, 0.95)
+    r = n * n // 8
+    # call 1 covers many tiles; call 2 fewer, so stale partials of call 1 remain
+    # in the shared array beyond what call 2 writes
+    for H, W, seed in ((1024, 2048, 41), (192, 544, 42)):
+        img = si.ar1_image(H, W, 0.9, seed)
+        (z0, r0, s0, p0), (z1, r1, s1, p1) = _both(rk, plan, img, r)
+        assert np.all(np.abs(z1 - z0) <= COEF_REL * np.maximum(np.abs(z0), 1.0))
+        assert np.array_equal(r1, r0)
+        assert abs(s1 - s0) <= SSE_REL * s0
+        assert abs(p1 - p0) <= 1e-3
+        # same kernel, same per-tile partials: in fact bit-identical
+        assert np.array_equal(z1, z0) and s1 == s0 and p1 == p0
+        assert math.isfinite(p1)
+
+
+def test_noalloc_rejects_oversized_images(rk):
+    plan = rk.rklt_make(8, 0.95)
+    d = ctypes.c_void_p(256)   # never dereferenced: the size check fails first
+    H, W = 32768 + 64, 32768   # 513 x 128 = 65664 tiles > 65536
+    st = rk.lib.rklt_fused_noalloc(plan.handle, d, H, W, W, 8, None, None, 0, d, d, None)
+    assert st == 1
+    assert b"too large" in rk.lib.rklt_last_error()
