@@ -4,8 +4,11 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+
 #include <cstdint>
+#include <cstring>
 
 namespace rklt {
 
@@ -163,6 +166,38 @@ __device__ __forceinline__ void named_sync(int id, int count) {
 // --------------------------------------------------------------------------
 // Byte k of a 32-bit word as an exact float.
 __device__ __forceinline__ float byte_f(uint32_t w, int k) { return float((w >> (8 * k)) & 0xffu); }
+
+// Packed binary16 pairs held in 32-bit registers.
+__device__ __forceinline__ __half2 as_h2(uint32_t u) {
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+__device__ __forceinline__ uint32_t as_u32(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// Bytes c0 and c1 of w as the pair (1024 + b0, 1024 + b1) of binary16 values:
+// 0x64 in the high byte of each lane makes the half 1024 + byte exactly.
+__device__ __forceinline__ uint32_t bytes_to_biased_h2(uint32_t w, int c0, int c1) {
+    return __byte_perm(w, 0x6464u, uint32_t(c0) | (4u << 4) | (uint32_t(c1) << 8) | (5u << 12));
+}
+
+// FP32 difference (half a) - (float c) with a single rounding (mixed-precision sub).
+__device__ __forceinline__ float sub_h_f(__half a, float c) {
+    float d;
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(a)), "f"(c));
+    return d;
+}
+
+// clip(floor(x), 0, 255) as an integer 0..255 (float-to-integer conversions saturate).
+__device__ __forceinline__ uint32_t floor_sat_u8(float x) {
+    uint32_t u;
+    asm("cvt.rmi.sat.u8.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return u;
+}
 
 // clip(floor(x + 1/2), 0, 255): round-half-up then saturate to 8 bits.
 __device__ __forceinline__ uint32_t recon_byte(float x) {

@@ -51,42 +51,55 @@ constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies alrea
 
 // ---------------------------------------------------------------------------
 // Register path: one N x N block per thread.  D is a compile-time constant.
+//
+// The column pass runs on packed binary16 pairs (two columns per instruction):
+// pixels, their mirrored sums (<= 510) and differences, and every partial sum of
+// T A (|.| <= N * 255 <= 2040) are integers below 2048, which binary16 represents
+// exactly, so the pass is still exact.  The row pass, the inverse and the error
+// run in FP32; the error takes each pixel straight from its exact half with a
+// mixed-precision subtraction.
 // ---------------------------------------------------------------------------
 template <int N, int D>
 __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
                                            bool recon) {
     constexpr int H2 = N / 2;
-    constexpr int W32 = N / 4;          // 32-bit words per block row
+    constexpr int NP = N / 2;           // column pairs
     constexpr int DR = D < N ? D : N;   // rows / columns of C that carry retained terms
     constexpr int DA = DR > 0 ? DR : 1; // array extent (D = 0 keeps nothing)
-    uint32_t raw[N][W32];
+    const __half2 k1024 = __float2half2_rn(1024.0f);
+    uint32_t w[N][N / 4];  // the block's bytes, 4 pixels per word
 #pragma unroll
     for (int k = 0; k < N; k++) {
         if constexpr (N == 8) {
-            const uint2 w = *reinterpret_cast<const uint2 *>(blk + k * TW);
-            raw[k][0] = w.x;
-            raw[k][1] = w.y;
+            const uint2 v = *reinterpret_cast<const uint2 *>(blk + k * TW);
+            w[k][0] = v.x;
+            w[k][1] = v.y;
         } else {
-            raw[k][0] = *reinterpret_cast<const uint32_t *>(blk + k * TW);
+            w[k][0] = *reinterpret_cast<const uint32_t *>(blk + k * TW);
         }
     }
-    // column transform: Y = T A, rows i < DR
+    // pixels (A[k][2p], A[k][2p+1]) of column pair p as exact binary16 pairs
+    auto px = [&](int k, int p) -> __half2 {
+        return __hsub2(as_h2(bytes_to_biased_h2(w[k][p >> 1], (2 * p) & 3, (2 * p + 1) & 3)), k1024);
+    };
+    // column transform Y = T A (rows i < DR), two columns per instruction
     float Y[DA][N];
 #pragma unroll
-    for (int c = 0; c < N; c++) {
-        float s[H2], d[H2];
+    for (int p = 0; p < NP; p++) {
+        __half2 sp[H2], dp[H2];
 #pragma unroll
         for (int j = 0; j < H2; j++) {
-            const float top = byte_f(raw[j][c >> 2], c & 3), bot = byte_f(raw[N - 1 - j][c >> 2], c & 3);
-            s[j] = top + bot;
-            d[j] = top - bot;
+            const __half2 top = px(j, p), bot = px(N - 1 - j, p);
+            sp[j] = __hadd2(top, bot);
+            dp[j] = __hsub2(top, bot);
         }
 #pragma unroll
         for (int i = 0; i < DR; i++) {
-            float acc = 0.0f;
+            __half2 acc = __hmul2(as_h2(P.T2[i][0]), (i & 1) ? dp[0] : sp[0]);
 #pragma unroll
-            for (int j = 0; j < H2; j++) acc = fmaf(P.T[i][j], (i & 1) ? d[j] : s[j], acc);
-            Y[i][c] = acc;
+            for (int j = 1; j < H2; j++) acc = __hfma2(as_h2(P.T2[i][j]), (i & 1) ? dp[j] : sp[j], acc);
+            Y[i][2 * p] = __low2float(acc);
+            Y[i][2 * p + 1] = __high2float(acc);
         }
     }
     // row transform: C = Y T^T on the support i + j < D; zonal mask on the last diagonal
@@ -152,42 +165,53 @@ __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int 
         }
     }
     // inverse column transform A'[k][c] = sum_i T^{-1}[k][i] X[i][c], one mirrored row
-    // pair (k, N-1-k) at a time; error; 8-bit output
-    float sse = 0.0f;
+    // pair (k, N-1-k) at a time, two columns per packed-FP32 instruction; error;
+    // 8-bit output clip(floor(A' + 1/2), 0, 255)
+    float2 sse2 = make_float2(0.0f, 0.0f);
+    const float2 half2f = make_float2(0.5f, 0.5f), neg1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
     for (int k = 0; k < H2; k++) {
-        uint32_t ot[W32], ob[W32];
+        uint32_t wt[N / 4], wb[N / 4];
 #pragma unroll
-        for (int w = 0; w < W32; w++) ot[w] = ob[w] = 0u;
+        for (int q = 0; q < N / 4; q++) {
+            uint32_t bt[4], bb[4];
 #pragma unroll
-        for (int c = 0; c < N; c++) {
-            float e = 0.0f, o = 0.0f;
+            for (int h = 0; h < 2; h++) {
+                const int p = 2 * q + h;
+                float2 e2 = make_float2(0.0f, 0.0f), o2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int i = 0; i < DR; i++) {
-                if (i & 1) o = fmaf(P.Ti[k][i], X[i][c], o);
-                else e = fmaf(P.Ti[k][i], X[i][c], e);
+                for (int i = 0; i < DR; i++) {
+                    const float t = P.Ti[k][i];
+                    const float2 x2 = make_float2(X[i][2 * p], X[i][2 * p + 1]);
+                    if (i & 1) o2 = __ffma2_rn(make_float2(t, t), x2, o2);
+                    else e2 = __ffma2_rn(make_float2(t, t), x2, e2);
+                }
+                const float2 top = __fadd2_rn(e2, o2), bot = __ffma2_rn(o2, neg1, e2);
+                const __half2 at2 = px(k, p), ab2 = px(N - 1 - k, p);
+                const float2 et = make_float2(sub_h_f(__low2half(at2), top.x), sub_h_f(__high2half(at2), top.y));
+                const float2 eb = make_float2(sub_h_f(__low2half(ab2), bot.x), sub_h_f(__high2half(ab2), bot.y));
+                sse2 = __ffma2_rn(et, et, sse2);
+                sse2 = __ffma2_rn(eb, eb, sse2);
+                const float2 vt = __fadd2_rn(top, half2f), vb = __fadd2_rn(bot, half2f);
+                bt[2 * h] = floor_sat_u8(vt.x);
+                bt[2 * h + 1] = floor_sat_u8(vt.y);
+                bb[2 * h] = floor_sat_u8(vb.x);
+                bb[2 * h + 1] = floor_sat_u8(vb.y);
             }
-            const float top = e + o, bot = e - o;
-            const float et = byte_f(raw[k][c >> 2], c & 3) - top;
-            const float eb = byte_f(raw[N - 1 - k][c >> 2], c & 3) - bot;
-            sse = fmaf(et, et, sse);
-            sse = fmaf(eb, eb, sse);
-            if (recon) {
-                ot[c >> 2] |= recon_byte(top) << (8 * (c & 3));
-                ob[c >> 2] |= recon_byte(bot) << (8 * (c & 3));
-            }
+            wt[q] = __byte_perm(__byte_perm(bt[0], bt[1], 0x0040), __byte_perm(bt[2], bt[3], 0x0040), 0x5410);
+            wb[q] = __byte_perm(__byte_perm(bb[0], bb[1], 0x0040), __byte_perm(bb[2], bb[3], 0x0040), 0x5410);
         }
         if (recon) {
             if constexpr (N == 8) {
-                *reinterpret_cast<uint2 *>(blk + k * TW) = make_uint2(ot[0], ot[1]);
-                *reinterpret_cast<uint2 *>(blk + (N - 1 - k) * TW) = make_uint2(ob[0], ob[1]);
+                *reinterpret_cast<uint2 *>(blk + k * TW) = make_uint2(wt[0], wt[1]);
+                *reinterpret_cast<uint2 *>(blk + (N - 1 - k) * TW) = make_uint2(wb[0], wb[1]);
             } else {
-                *reinterpret_cast<uint32_t *>(blk + k * TW) = ot[0];
-                *reinterpret_cast<uint32_t *>(blk + (N - 1 - k) * TW) = ob[0];
+                *reinterpret_cast<uint32_t *>(blk + k * TW) = wt[0];
+                *reinterpret_cast<uint32_t *>(blk + (N - 1 - k) * TW) = wb[0];
             }
         }
     }
-    return sse;
+    return sse2.x + sse2.y;
 }
 
 template <int N>
@@ -377,6 +401,204 @@ __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g
     return sse;
 }
 
+// ---------------------------------------------------------------------------
+// Cooperative path for N = 16 and 32.  All block-rows of the tile (R = 64/N of
+// them, NB = 256/N blocks each) are transformed together in three phases
+// separated by barriers:
+//   1. column pass: a thread takes two adjacent columns of one block-row and forms
+//      Y = T A for rows i < Dr with packed-FP32 FMAs; Y goes to Ys;
+//   2. row pass + inverse row pass: a thread takes one row i of one block; it forms
+//      C[i][j] for i + j < D (masked to the first r zig-zag positions), stages the
+//      normalised coefficients in Zs, and writes X[i][.] = sum_j C[i][j] T^{-1}[.][j]
+//      back over its row of Ys.  Tasks are ordered by i so that each warp shares i
+//      and the triangular bound j < D - i stays warp-uniform;
+//   3. inverse column pass, two columns per thread: A' = T^{-1} X, error, 8-bit
+//      output in place.
+// Ys holds rows i < Dr of every block: index ((round * Dr + i) * NB + b) * (N + 4) + c,
+// rows 16-byte aligned and padded by 4 floats per block against bank conflicts.
+// ---------------------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int coop2_rounds() { return TH / N; }
+
+__host__ __device__ inline bool coop2_stage_coef(int N, int r) {
+    return int64_t(TH / N) * (TW / N) * r * 4 <= 32 * 1024;
+}
+
+template <int N, int DRM>
+__device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
+                                            int ct, float *Ys, float *Zs) {
+    constexpr int H2 = N / 2;
+    constexpr int R = TH / N;
+    constexpr int NB = TW / N;
+    constexpr int LB = N + 4;  // padded block row in Ys
+    const TileCoord tc = tile_coord(g, tile_id);
+    const int bw = g.W / N;
+    const int D = g.D, r = g.r;
+    const int Dr = D < N ? D : N;
+    const bool stage = coop2_stage_coef(N, r);
+    const int rows_in = min(R, (g.H - tc.ty * TH) / N);  // block-rows of this tile inside the image
+    const int nb_in = min(NB, bw - tc.tx * NB);           // blocks per block-row inside the image
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    const float2 bias24 = make_float2(-16777216.0f, -16777216.0f);
+    float sse = 0.0f;
+
+    // ---- phase 1: column pass, two columns per task
+    for (int t = ct; t < R * (TW / 2); t += NCONS) {
+        const int round = t / (TW / 2), cp = t - round * (TW / 2);
+        if (round >= rows_in) continue;
+        const int b = (2 * cp) / N, cc = (2 * cp) - b * N;
+        const uint8_t *col = tile + round * N * TW + 2 * cp;
+        float2 sp[H2], dp[H2];
+#pragma unroll
+        for (int j = 0; j < H2; j++) {
+            const uint32_t top = *reinterpret_cast<const uint16_t *>(col + j * TW);
+            const uint32_t bot = *reinterpret_cast<const uint16_t *>(col + (N - 1 - j) * TW);
+            // biased floats 2^23 + byte (exact); s = (t - 2^24) + b is exact, d = t - b is exact
+            const float2 tf = make_float2(__uint_as_float(0x4B000000u | (top & 0xffu)),
+                                          __uint_as_float(0x4B000000u | (top >> 8)));
+            const float2 bf = make_float2(__uint_as_float(0x4B000000u | (bot & 0xffu)),
+                                          __uint_as_float(0x4B000000u | (bot >> 8)));
+            sp[j] = __fadd2_rn(__fadd2_rn(tf, bias24), bf);
+            dp[j] = __ffma2_rn(bf, neg1, tf);
+        }
+        float *dst = Ys + (round * Dr * NB + b) * LB + cc;
+#pragma unroll
+        for (int i = 0; i < DRM; i++) {
+            if (i < Dr) {
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int j = 0; j < H2; j++) {
+                    const float tv = P.T[i][j];
+                    acc = __ffma2_rn(make_float2(tv, tv), (i & 1) ? dp[j] : sp[j], acc);
+                }
+                *reinterpret_cast<float2 *>(dst + i * NB * LB) = acc;
+            }
+        }
+    }
+    named_sync(1, NCONS);
+
+    // ---- phase 2: row pass, coefficients, inverse row pass; one (block, row) per task
+    for (int t = ct; t < R * NB * Dr; t += NCONS) {
+        const int i = t / (R * NB), rb = t - i * (R * NB);
+        const int round = rb / NB, b = rb - round * NB;
+        if (round >= rows_in || b >= nb_in) continue;
+        float *row = Ys + ((round * Dr + i) * NB + b) * LB;
+        float s[H2], d[H2];
+#pragma unroll
+        for (int l4 = 0; l4 < N / 8; l4++) {
+            const float4 lo = *reinterpret_cast<const float4 *>(row + 4 * l4);
+            const float4 hi = *reinterpret_cast<const float4 *>(row + N - 4 - 4 * l4);
+            // lo holds Y[4l4 .. 4l4+3], hi holds Y[N-4-4l4 .. N-1-4l4]
+            s[4 * l4 + 0] = lo.x + hi.w; d[4 * l4 + 0] = lo.x - hi.w;
+            s[4 * l4 + 1] = lo.y + hi.z; d[4 * l4 + 1] = lo.y - hi.z;
+            s[4 * l4 + 2] = lo.z + hi.y; d[4 * l4 + 2] = lo.z - hi.y;
+            s[4 * l4 + 3] = lo.w + hi.x; d[4 * l4 + 3] = lo.w - hi.x;
+        }
+        float xe[H2], xo[H2];
+#pragma unroll
+        for (int l = 0; l < H2; l++) xe[l] = xo[l] = 0.0f;
+        const int jmax = D - i;
+        const float si = P.s[i];
+        float *zs = Zs + (round * NB + b) * r;
+        float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
+                                         int64_t(tc.ty * R + round) * bw + tc.tx * NB + b) * r
+                            : nullptr;
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            if (j < jmax) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int l = 0; l < H2; l++) acc = fmaf(P.T[j][l], (j & 1) ? d[l] : s[l], acc);
+                const int z = zz_index(N, i, j);
+                const bool keep = z < r;
+                const float c = keep ? acc : 0.0f;
+                if (keep) {
+                    const float bval = (si * P.s[j]) * c;
+                    if (stage) zs[z] = bval;
+                    else if (zg) zg[z] = bval;
+                }
+#pragma unroll
+                for (int l = 0; l < H2; l++) {
+                    if (j & 1) xo[l] = fmaf(c, P.Ti[l][j], xo[l]);
+                    else xe[l] = fmaf(c, P.Ti[l][j], xe[l]);
+                }
+            }
+        }
+#pragma unroll
+        for (int l4 = 0; l4 < N / 8; l4++) {
+            float4 lo, hi;
+            lo.x = xe[4 * l4 + 0] + xo[4 * l4 + 0]; hi.w = xe[4 * l4 + 0] - xo[4 * l4 + 0];
+            lo.y = xe[4 * l4 + 1] + xo[4 * l4 + 1]; hi.z = xe[4 * l4 + 1] - xo[4 * l4 + 1];
+            lo.z = xe[4 * l4 + 2] + xo[4 * l4 + 2]; hi.y = xe[4 * l4 + 2] - xo[4 * l4 + 2];
+            lo.w = xe[4 * l4 + 3] + xo[4 * l4 + 3]; hi.x = xe[4 * l4 + 3] - xo[4 * l4 + 3];
+            *reinterpret_cast<float4 *>(row + 4 * l4) = lo;
+            *reinterpret_cast<float4 *>(row + N - 4 - 4 * l4) = hi;
+        }
+    }
+    named_sync(1, NCONS);
+
+    // ---- staged coefficients: each block-row's blocks are contiguous in the output
+    if (stage && g.zcoef) {
+        for (int round = 0; round < rows_in; round++) {
+            float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * R + round) * bw +
+                                    tc.tx * NB) * r;
+            const float *src = Zs + round * NB * r;
+            for (int q = ct; q < nb_in * r; q += NCONS) dst[q] = src[q];
+        }
+    }
+
+    // ---- phase 3: inverse column pass, two columns per task; error; 8-bit output in place
+    const float2 half2f = make_float2(0.5f, 0.5f);
+    const float2 bias23 = make_float2(-8388608.0f, -8388608.0f);
+    const int x_in = g.W - tc.tx * TW;  // columns of this tile inside the image
+    for (int t = ct; t < R * (TW / 2); t += NCONS) {
+        const int round = t / (TW / 2), cp = t - round * (TW / 2);
+        if (round >= rows_in) continue;
+        const int b = (2 * cp) / N, cc = (2 * cp) - b * N;
+        const bool col_in = 2 * cp < x_in;  // W is a multiple of N, so both columns are in or out
+        uint8_t *col = tile + round * N * TW + 2 * cp;
+        const float *src = Ys + (round * Dr * NB + b) * LB + cc;
+        float2 xv[DRM];
+#pragma unroll
+        for (int i = 0; i < DRM; i++)
+            xv[i] = (i < Dr) ? *reinterpret_cast<const float2 *>(src + i * NB * LB) : make_float2(0.0f, 0.0f);
+        float2 sse2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < H2; k++) {
+            float2 e2 = make_float2(0.0f, 0.0f), o2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int i = 0; i < DRM; i++) {
+                if (i < Dr) {
+                    const float tv = P.Ti[k][i];
+                    if (i & 1) o2 = __ffma2_rn(make_float2(tv, tv), xv[i], o2);
+                    else e2 = __ffma2_rn(make_float2(tv, tv), xv[i], e2);
+                }
+            }
+            const float2 top = __fadd2_rn(e2, o2), bot = __ffma2_rn(o2, neg1, e2);
+            uint16_t *pt = reinterpret_cast<uint16_t *>(col + k * TW);
+            uint16_t *pb = reinterpret_cast<uint16_t *>(col + (N - 1 - k) * TW);
+            const uint32_t wt = *pt, wb = *pb;
+            if (col_in) {
+                const float2 at = __fadd2_rn(make_float2(__uint_as_float(0x4B000000u | (wt & 0xffu)),
+                                                         __uint_as_float(0x4B000000u | (wt >> 8))), bias23);
+                const float2 ab = __fadd2_rn(make_float2(__uint_as_float(0x4B000000u | (wb & 0xffu)),
+                                                         __uint_as_float(0x4B000000u | (wb >> 8))), bias23);
+                const float2 et = __ffma2_rn(top, neg1, at), eb = __ffma2_rn(bot, neg1, ab);
+                sse2 = __ffma2_rn(et, et, sse2);
+                sse2 = __ffma2_rn(eb, eb, sse2);
+            }
+            if (g.recon) {
+                const float2 vt = __fadd2_rn(top, half2f), vb = __fadd2_rn(bot, half2f);
+                *pt = uint16_t(floor_sat_u8(vt.x) | (floor_sat_u8(vt.y) << 8));
+                *pb = uint16_t(floor_sat_u8(vb.x) | (floor_sat_u8(vb.y) << 8));
+            }
+        }
+        sse += sse2.x + sse2.y;
+    }
+    named_sync(1, NCONS);  // Ys / Zs are reused by the next tile
+    return sse;
+}
+
 template <int N>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
                                               int ct, float *Ys, float *Zs) {
@@ -386,8 +608,19 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         if (g.D <= REG_DMAX8) return tile_reg<8>(P, g, tile, tile_id, ct);
         return tile_coop<8>(P, g, tile, tile_id, ct, Ys, Zs);
     } else {
-        return tile_coop<N>(P, g, tile, tile_id, ct, Ys, Zs);
+        const int Dr = g.D < N ? g.D : N;
+        if (Dr <= N / 4) return tile_coop2<N, N / 4>(P, g, tile, tile_id, ct, Ys, Zs);
+        if (Dr <= N / 2) return tile_coop2<N, N / 2>(P, g, tile, tile_id, ct, Ys, Zs);
+        return tile_coop2<N, N>(P, g, tile, tile_id, ct, Ys, Zs);
     }
+}
+
+// Sum of the eight consumer warps' partials of one tile, in warp order.
+__device__ __forceinline__ float sum_warp_partials(const float *w) {
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NCONS / 32; i++) t += w[i];
+    return t;
 }
 
 // Fixed-order reduction over the consumer threads; thread 0 returns the sum.
@@ -422,11 +655,17 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
     SmemLayout L{};
     L.bar_off = stages * TILE_BYTES;
     L.red_off = L.bar_off + 2 * STAGES * 8;
-    L.ys_off = L.red_off + 64;
-    const bool coop = (N >= 16) || (N == 8 && D > REG_DMAX8);
-    const int ys = coop ? N * LDY * 4 : 0;
+    L.ys_off = L.red_off + STAGES * (NCONS / 32) * 4;  // barrier and reduction slots for the deepest ring
+    int ys = 0, zs = 0;
+    if (N >= 16) {
+        const int Dr = D < N ? D : N;
+        ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
+        zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * r * 4 : 0;
+    } else if (N == 8 && D > REG_DMAX8) {
+        ys = N * LDY * 4;
+        zs = (TW / N) * r * 4;
+    }
     L.zs_off = L.ys_off + ((ys + 15) / 16) * 16;
-    const int zs = coop ? (TW / N) * r * 4 : 0;
     L.total = L.zs_off + zs + 1024;  // + slack for aligning the dynamic base
     return L;
 }
@@ -440,7 +679,8 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                  const __grid_constant__ CUtensorMap tm_out, const FusedGeom g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const SmemLayout L = smem_layout<N>(g.use_tma ? STAGES : 1, g.r, g.D);
+    const int NST = g.stages;  // ring depth (<= STAGES)
+    const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *empty = full + STAGES;
     float *red = reinterpret_cast<float *>(smem + L.red_off);
@@ -449,7 +689,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     const int tid = threadIdx.x;
 
     if (g.use_tma && tid == NCONS) {
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < NST; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NCONS / 32);
         }
@@ -463,16 +703,18 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
         int64_t it = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
-            const int s = int(it % STAGES);
-            if (it >= STAGES) {
+            const int s = int(it % NST);
+            if (it >= NST) {
                 // slot s last held tile (it - STAGES): wait for its release, write it back
-                if (!mbar_wait_bounded(&empty[s], uint32_t(((it / STAGES) - 1) & 1), g.timeout_ns)) {
+                if (!mbar_wait_bounded(&empty[s], uint32_t(((it / NST) - 1) & 1), g.timeout_ns)) {
                     ok = false;
                     break;
                 }
+                const int64_t prev = tile - int64_t(NST) * gridDim.x;
+                g.partials[prev] = sum_warp_partials(red + s * (NCONS / 32));
                 if (g.recon) {
                     int x, y, z;
-                    tile_origin(g, tile - int64_t(STAGES) * gridDim.x, x, y, z);
+                    tile_origin(g, prev, x, y, z);
                     tma_store_3d(&tm_out, x, y, z, smem + s * TILE_BYTES);
                     bulk_commit();
                     bulk_wait_read_all();  // the store has read the slot before it is refilled
@@ -486,18 +728,20 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
         }
         // drain: write back the slots still holding consumed tiles
         const int64_t issued = it;
-        for (int64_t j = issued > STAGES ? issued - STAGES : 0; j < issued; j++) {
-            const int s = int(j % STAGES);
-            const uint32_t par = uint32_t((j / STAGES) & 1);
+        for (int64_t j = issued > NST ? issued - NST : 0; j < issued; j++) {
+            const int s = int(j % NST);
+            const uint32_t par = uint32_t((j / NST) & 1);
             if (!ok || !mbar_wait_bounded(&empty[s], par, g.timeout_ns)) {
                 // the consumers gave up: let this slot's load land before the CTA exits
                 ok = false;
                 if (!g.inject_stall) mbar_wait_bounded(&full[s], par, DRAIN_NS);
                 continue;
             }
+            const int64_t tj = int64_t(blockIdx.x) + j * gridDim.x;
+            g.partials[tj] = sum_warp_partials(red + s * (NCONS / 32));
             if (g.recon) {
                 int x, y, z;
-                tile_origin(g, int64_t(blockIdx.x) + j * gridDim.x, x, y, z);
+                tile_origin(g, tj, x, y, z);
                 tma_store_3d(&tm_out, x, y, z, smem + s * TILE_BYTES);
                 bulk_commit();
             }
@@ -510,16 +754,18 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     const bool al8 = ((reinterpret_cast<uintptr_t>(g.img) | uintptr_t(g.ld) | uintptr_t(g.img_stride)) & 7) == 0;
     const bool al8o =
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
+    // the cooperative path synchronises the consumer warps with named barriers, so
+    // they must give up together; the register path has no such barrier
+    const bool coop = (N >= 16) || (N == 8 && g.D > REG_DMAX8);
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
         uint8_t *buf;
         int s = 0;
         int x0 = 0, y0 = 0, z = 0, hv = 0, wv = 0;
         if (g.use_tma) {
-            s = int(it % STAGES);
-            const bool got = mbar_wait_bounded(&full[s], uint32_t((it / STAGES) & 1), g.timeout_ns);
-            // all consumers leave together if any of them gave up (they share named barriers)
-            if (named_any(3, NCONS, !got)) break;
+            s = int(it % NST);
+            const bool got = mbar_wait_bounded(&full[s], uint32_t((it / NST) & 1), g.timeout_ns);
+            if (coop ? named_any(3, NCONS, !got) : !got) break;
             buf = smem + s * TILE_BYTES;
         } else {
             buf = smem;
@@ -550,14 +796,19 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             }
             named_sync(1, NCONS);
         }
-        const float v = process_tile<N>(P, g, buf, tile, tid, Ys, Zs);
+        float v = process_tile<N>(P, g, buf, tile, tid, Ys, Zs);
         if (g.use_tma) {
+            // warp partial -> red[s][warp]; the producer sums the eight in order
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if ((tid & 31) == 0) red[s * (NCONS / 32) + (tid >> 5)] = v;
             if (g.recon) fence_proxy_async_smem();
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+        } else {
+            const float t = reduce_consumers(v, red, tid);
+            if (tid == 0) g.partials[tile] = t;
         }
-        const float t = reduce_consumers(v, red, tid);
-        if (tid == 0) g.partials[tile] = t;
         if (!g.use_tma && g.recon) {
             named_sync(1, NCONS);
             uint8_t *dst = g.recon + int64_t(z) * g.recon_stride + int64_t(y0) * g.ld_recon + x0;
@@ -665,7 +916,8 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    const SmemLayout L = smem_layout<N>(tma ? STAGES : 1, a.r, g.D);
+    g.stages = (N >= 16) ? 3 : STAGES;
+    const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D);
     const int dev = ensure_smem_attr(reinterpret_cast<const void *>(fused_kernel<N>));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<N>, NCONS + 32, L.total);

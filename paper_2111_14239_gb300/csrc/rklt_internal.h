@@ -30,6 +30,7 @@ struct PlanK {
     float Tih[N / 2][N];  // That^{-1}[l][j] = T^{-1}[l][j] / s_j
     float sij[N][N];      // s_i * s_j (B = sij o C), rounded once from FP64
     float s[N];           // s_i
+    uint32_t T2[N][N / 2]; // T[i][j] as a packed pair of IEEE halves (both lanes equal)
 };
 
 // Host-side plan object behind the opaque rklt_plan handle.
@@ -60,6 +61,7 @@ struct FusedGeom {
     int r, D;                    // retained coefficients, diagonal bound
     int coef_vec4;               // r % 4 == 0 and zcoef 16-byte aligned
     int use_tma;                 // tiles move by TMA (else plain loads)
+    int stages;                  // TMA ring depth
     int inject_stall;            // test hook: the producer issues no loads
     uint64_t timeout_ns;
 };

@@ -122,6 +122,13 @@ void fill_kparams(Plan &p) {
     for (int i = 0; i < M; i++)
         for (int j = 0; j < M; j++) k.sij[i][j] = float(p.s[i] * p.s[j]);
     for (int i = 0; i < M; i++) k.s[i] = float(p.s[i]);
+    // 0, +1, -1 as binary16: 0x0000, 0x3C00, 0xBC00, duplicated into both lanes
+    for (int i = 0; i < M; i++)
+        for (int j = 0; j < M / 2; j++) {
+            const int t = p.T[size_t(i) * M + j];
+            const uint32_t h = t == 0 ? 0x0000u : (t > 0 ? 0x3C00u : 0xBC00u);
+            k.T2[i][j] = h | (h << 16);
+        }
 }
 
 // Validate an integer matrix and complete the plan: S (Eq. 1), T^{-1}, tables.
