@@ -34,7 +34,14 @@ NIMG, SIDE = 16, 4096
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by kernel; None until a capture of the current kernel exists.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
+    # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
+    "fused_kernel<4>": 268512768 + 344303616,
+    "fused_kernel<8>": 268518656 + 346935552,
+    "fused_kernel<16>": 268571136 + 342560256,
+    "fused_kernel<32>": 269329920 + 356632320,
+}
 
 
 def peaks():
@@ -291,6 +298,18 @@ def run_ours(args):
         v, cores, sample = oracle_sample(imgs_np, budget_s=args.ref_budget)
         cpu = {"value": v, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    workloads = {}
+    if world == 1 and not args.no_extras:
+        for name, fn in (("single_512", lambda: leg_single(rk, dev, stream)),
+                         ("r_sweep_256x512", lambda: leg_sweep(rk, dev, stream)),
+                         ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream)),
+                         ("serving", lambda: leg_serve(rk, dev, args.serve_seconds))):
+            try:
+                workloads[name] = fn()
+            except Exception as e:  # report, do not lose the main line
+                workloads[name] = {"error": repr(e)}
+        rk.rklt_device_status()
+
     line = {
         "metric": "Mpixel/s fwd+zonal+inv+PSNR",
         "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -309,11 +328,125 @@ def run_ours(args):
         "gpu_launches": 2 * len(NS) * args.steps,
         "clocks": clk.summary(),
         "psnr_sample_db": psnr,
+        "workloads": workloads,
     }
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
+
+
+# ---------------------------------------------------------------------------
+# Extra workloads, measured after the main timed region (single GPU only)
+# ---------------------------------------------------------------------------
+def _time_ms(fn, reps, stream):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def leg_single(rk, dev, stream):
+    """One 512 x 512 image (rho 0.95, seed 0), N = 8, r = 10: per-call latency."""
+    import torch
+    import synth_inputs as si
+    img = torch.from_numpy(si.single_512()).to(dev)
+    plan = rk.rklt_make(8, 0.95)
+    zc = torch.empty((64 * 64, 10), device=dev)
+    rec = torch.empty_like(img)
+    sse = torch.empty(1, dtype=torch.float64, device=dev)
+    ps = torch.empty(1, device=dev)
+    ms = _time_ms(lambda: rk.rklt_fused(plan, img, 10, sse, ps, zcoef=zc, recon=rec, stream=stream), 200, stream)
+    return {"workload": "1 x 512x512, N=8, rho=0.95, r=10, fwd+zonal+inv+PSNR", "us_per_image": ms * 1e3,
+            "mpixel_per_s": 512 * 512 / (ms / 1e3) / 1e6, "psnr_db": round(float(ps.item()), 4)}
+
+
+def leg_sweep(rk, dev, stream):
+    """256 images of 512 x 512 (rho ~ U(0.80, 0.98)), N = 8 plans for the 10 grid rho,
+    PSNR for every r = 1..64."""
+    import torch
+    import synth_inputs as si
+    imgs, _ = si.sweep_batch(256, 512, 1000)
+    d = torch.from_numpy(imgs).to(dev)
+    plans = [rk.rklt_make(8, rho) for rho in si.GRID_RHOS]
+    ps = torch.empty((256, len(plans), 64), device=dev)
+    ms = _time_ms(lambda: rk.rklt_rsweep(plans, d, None, ps, stream=stream), 10, stream)
+    return {"workload": "256 x 512x512 AR(1), 10 plans (4 distinct T), r = 1..64", "ms_per_sweep": ms,
+            "mpixel_per_s": imgs.size / (ms / 1e3) / 1e6,
+            "psnr_values_per_s": 256 * len(plans) * 64 / (ms / 1e3),
+            "l2": "input 67 MB is L2-resident between repetitions",
+            "psnr_db_img0_T4_r10": round(float(ps[0, 9, 9].item()), 4)}
+
+
+def leg_batch(rk, dev, stream, n_images=2000):
+    """2000 AR(1) crops, sides U{64..4096 step 8}, rho ~ U(0.5, 0.98) -> nearest of the
+    10 grid RKLTs, N = 8, r ~ U{1..64}: one graph-replayed persistent batch against
+    one fused launch per image."""
+    import numpy as np
+    import torch
+    import synth_inputs as si
+    items = si.mixed_items(n_images)
+    need = sorted({si.nearest_grid_rho(it.rho) for it in items})
+    bases = si.base_fields(need, 4096, 6000)
+    hosts = si.mixed_batch(items, bases)
+    plans = [rk.rklt_make(8, rho) for rho in si.GRID_RHOS]
+    pidx = {rho: k for k, rho in enumerate(si.GRID_RHOS)}
+    bufs, entries = [], []
+    for it, h in zip(items, hosts):
+        d = torch.from_numpy(np.ascontiguousarray(h)).to(dev)
+        rec = torch.empty_like(d)
+        zc = torch.empty((it.h // 8) * (it.w // 8) * it.r, device=dev)
+        bufs.append((d, rec, zc))
+        entries.append((d, pidx[si.nearest_grid_rho(it.rho)], it.r, zc, rec))
+    item_arr = rk.make_items(entries)
+    sse_b = torch.empty(n_images, dtype=torch.float64, device=dev)
+    ps_b = torch.empty(n_images, device=dev)
+    batch = rk.rklt_batch_create(item_arr, plans, sse_b, ps_b, autotune=True)
+    ms_batch = _time_ms(lambda: batch.run(stream), 5, stream)
+    sse_p = torch.empty(n_images, dtype=torch.float64, device=dev)
+    ps_p = torch.empty(n_images, device=dev)
+
+    def plain():
+        for k, (it, (d, rec, zc)) in enumerate(zip(items, bufs)):
+            rk.rklt_fused(plans[entries[k][1]], d, it.r, sse_p[k:k + 1], ps_p[k:k + 1], zcoef=zc, recon=rec,
+                          stream=stream)
+    ms_plain = _time_ms(plain, 2, stream)
+    a, b = sse_b.cpu().numpy(), sse_p.cpu().numpy()
+    rel = float(np.max(np.abs(a - b) / np.maximum(b, 1e-30)))
+    px = sum(it.h * it.w for it in items)
+    info = batch.info()
+    batch.close()
+    return {"workload": f"{n_images} AR(1) crops, sides U{{64..4096/8}}, N=8, r~U{{1..64}}, nearest of 10 RKLTs",
+            "gpixel": px / 1e9, "graph_batch_ms": ms_batch, "plain_launches_ms": ms_plain,
+            "graph_batch_mpixel_per_s": px / (ms_batch / 1e3) / 1e6,
+            "plain_mpixel_per_s": px / (ms_plain / 1e3) / 1e6, "speedup": ms_plain / ms_batch,
+            "max_rel_sse_diff_vs_plain": rel, "autotuned": info}
+
+
+def leg_serve(rk, dev, duration_s=6.0, rate=2000.0):
+    """Poisson 2000 req/s; lognormal sides (median 768, sigma 0.5); rho in
+    {0.5, 0.8, 0.9, 0.95}; r ~ U{1..64}; 8 GB budget: continuous batching vs plain."""
+    import synth_inputs as si
+    from paper_2111_14239_gb300 import serve
+    rhos = (0.5, 0.8, 0.9, 0.95)
+    bases = si.base_fields(rhos, 4096, 6100)
+    pool = si.serving_pool(96, bases)
+    srv = serve.Server(rhos, budget_bytes=8 << 30, streams=4)
+    out = {"workload": f"Poisson arrivals, lognormal sides (median 768, sigma 0.5), N=8, "
+                       f"rho in {{0.5,0.8,0.9,0.95}}, r~U{{1..64}}, 8 GB budget; nominal {rate:.0f} req/s "
+                       f"for {duration_s:.0f} s and a 4x stress rate for {duration_s / 2:.0f} s"}
+    for tag, rr, dur in (("nominal", rate, duration_s), ("stress_4x", 4 * rate, duration_s / 2)):
+        cont = srv.run(serve.make_trace(rr, dur, pool, seed=5000, rhos=rhos))
+        plain = serve.serve_plain(srv.plans, serve.make_trace(rr, dur, pool, seed=5000, rhos=rhos))
+        out[tag] = {"rate_req_per_s": rr, "continuous_batching": cont, "plain_per_request": plain}
+    return out
 
 def main():
     ap = argparse.ArgumentParser()
@@ -325,6 +458,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--block-sizes", default="4,8,16,32", help="subset of N (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the single/sweep/batch/serving legs")
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

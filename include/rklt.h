@@ -167,6 +167,75 @@ rklt_status rklt_fused_batched(const rklt_plan *plan, const uint8_t *d_img, int 
                                uint8_t *d_recon, int64_t ld_recon, int64_t recon_stride,
                                double *d_sse, float *d_psnr, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Many images of uneven sizes, each with its own r and plan, in one pass
+ * (the batched form of Sec. 4.1's per-image compression).  N = 4 or 8.
+ * ------------------------------------------------------------------------ */
+
+/* One image of a batch.  d_img: H x W uint8, pitch ld bytes; image rows must be
+ * N-byte aligned (pointer and ld), as must the reconstruction's.  plan: index into
+ * the plans array of the call.  d_zcoef: [blocks][r] FP32 compact zig-zag
+ * coefficients (as rklt_fused) or NULL.  d_recon: uint8 reconstruction or NULL. */
+typedef struct rklt_item {
+    const uint8_t *d_img;
+    int H, W;
+    int64_t ld;
+    int plan;
+    int r;
+    float *d_zcoef;
+    uint8_t *d_recon;
+    int64_t ld_recon;
+} rklt_item;
+
+/* Immediate batched pass: items are grouped by plan; per group one launch of a
+ * persistent kernel over a flattened queue of 32-block units of all its images
+ * (warp per unit, each lane one block, coalesced row accesses), then a per-image
+ * SSE / PSNR kernel.  d_sse[i], d_psnr[i] receive item i's results; they are
+ * bit-identical to what a batch of item i alone produces.  Scratch (descriptors,
+ * per-unit partials) comes from a stream-ordered pool.  h_items may be reused as
+ * soon as the call returns.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED (N not 4 or 8,
+ * misaligned rows), RKLT_ERR_OOM, RKLT_ERR_CUDA. */
+rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,
+                             double *d_sse, float *d_psnr, void *stream);
+
+typedef struct rklt_batch rklt_batch;
+
+/* A reusable batch: the work queue (library-owned device memory, freed by
+ * rklt_batch_destroy) is built once, the launch sequence is captured into a CUDA
+ * graph and every rklt_batch_run replays it.  The device buffers named in h_items
+ * and d_sse / d_psnr are baked into the graph: refill them between runs, keep
+ * them alive until rklt_batch_destroy.  flags bit 0 = autotune: time a few launch
+ * shapes (threads per CTA, CTAs per SM) on the batch itself and keep the fastest;
+ * creation then runs the batch several times, overwriting its outputs.  Creation
+ * synchronises the device.
+ * Errors: as rklt_fused_items. */
+rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,
+                              double *d_sse, float *d_psnr, int flags, rklt_batch **out);
+
+/* Replay the batch's graph on `stream`.  Errors: RKLT_ERR_ARG, RKLT_ERR_CUDA. */
+rklt_status rklt_batch_run(rklt_batch *b, void *stream);
+
+/* The shape the batch runs with; tuned_us = best timed run (0 without autotune). */
+rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us);
+
+/* Wait for the batch's own stream, free its device memory and graph (NULL ignored). */
+void rklt_batch_destroy(rklt_batch *b);
+
+/* r-sweep: for nimg same-shape images and nplans plans (all with the same N, 4 or
+ * 8), the SSE and PSNR of the reconstruction that keeps the first r zig-zag
+ * coefficients, for every r = 1..N*N (Sec. 4.1 zonal retention swept over r, as
+ * in the paper's r in (0, 45) study).  Outputs are [image][plan][r - 1]:
+ * d_psnr (required) and d_sse (FP64, may be NULL); r = N*N gives SSE 0 and PSNR +inf.
+ * Per block the exact coefficients c_k are formed once and
+ * SSE(r) = SSE(r+1) + c_r (c_r G_rr + 2 sum_{l>r} c_l G_rl) with
+ * G_kl = H[i_k][i_l] H[j_k][j_l], H = (T T^T)^{-1} (Parseval when T T^T is
+ * diagonal); plans with identical T are evaluated once.  Image rows must be N-byte
+ * aligned.  Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED, RKLT_ERR_OOM,
+ * RKLT_ERR_CUDA. */
+rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, const uint8_t *d_imgs, int nimg, int H, int W,
+                        int64_t ld, int64_t img_stride, double *d_sse, float *d_psnr, void *stream);
+
 /* rklt_fused for callers that must not allocate.  (Not part of the paper: this
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *

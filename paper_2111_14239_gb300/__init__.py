@@ -20,7 +20,8 @@ from . import _build
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
     "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
-    "rklt_fused", "rklt_fused_batched", "rklt_fused_noalloc", "rklt_device_status", "rklt_set_wait_timeout_us",
+    "rklt_fused", "rklt_fused_batched", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
+    "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
 ]
 
@@ -29,6 +30,13 @@ STATUS = {0: "RKLT_OK", 1: "RKLT_ERR_ARG", 2: "RKLT_ERR_SHAPE", 3: "RKLT_ERR_DEG
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "rklt.h")
+
+
+class RklTItem(ctypes.Structure):
+    """rklt_item of include/rklt.h."""
+    _fields_ = [("d_img", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("ld", ctypes.c_int64),
+                ("plan", ctypes.c_int), ("r", ctypes.c_int), ("d_zcoef", ctypes.c_void_p),
+                ("d_recon", ctypes.c_void_p), ("ld_recon", ctypes.c_int64)]
 
 
 class RklTError(RuntimeError):
@@ -63,6 +71,12 @@ _SIGS = {
     "rklt_fused_batched": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P]),
     "rklt_fused_noalloc": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_device_status": (_I, []),
+    "rklt_fused_items": (_I, [_P, _I, _P, _I, _P, _P, _P]),
+    "rklt_batch_create": (_I, [_P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(_P)]),
+    "rklt_batch_run": (_I, [_P, _P]),
+    "rklt_batch_info": (_I, [_P, _P, _P, _P, _P]),
+    "rklt_batch_destroy": (None, [_P]),
+    "rklt_rsweep": (_I, [_P, _I, _P, _I, _I, _I, _L, _L, _P, _P, _P]),
     "rklt_set_wait_timeout_us": (None, [_U32]),
     "rklt_set_transport": (None, [_I]),
     "rklt_debug_inject_stall": (None, [_I]),
@@ -229,6 +243,81 @@ def rklt_fused_batched(plan: Plan, imgs, r: int, sse, psnr, zcoef=None, recon=No
         ldr, rstr = 0, 0
     _check(lib.rklt_fused_batched(plan.handle, imgs.data_ptr(), nimg, H, W, ld, istr, r, _ptr(zcoef), _ptr(recon),
                                   ldr, rstr, _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+def make_items(entries):
+    """entries: iterable of (img 2-D uint8 tensor, plan_index, r, zcoef tensor|None, recon tensor|None)."""
+    entries = list(entries)
+    arr = (RklTItem * len(entries))()
+    for k, (img, plan, r, zc, rec) in enumerate(entries):
+        assert img.dim() == 2 and img.stride(1) == 1
+        arr[k].d_img = img.data_ptr()
+        arr[k].H, arr[k].W = img.shape
+        arr[k].ld = img.stride(0)
+        arr[k].plan = plan
+        arr[k].r = r
+        arr[k].d_zcoef = zc.data_ptr() if zc is not None else None
+        arr[k].d_recon = rec.data_ptr() if rec is not None else None
+        arr[k].ld_recon = rec.stride(0) if rec is not None else 0
+    return arr
+
+
+def _plan_array(plans):
+    arr = (ctypes.c_void_p * len(plans))()
+    for k, p in enumerate(plans):
+        arr[k] = p.handle.value
+    return arr
+
+
+def rklt_fused_items(items, plans, sse, psnr, stream=None):
+    """items: make_items(...) array; plans: list of Plan."""
+    _check(lib.rklt_fused_items(ctypes.cast(items, ctypes.c_void_p), len(items),
+                                ctypes.cast(_plan_array(plans), ctypes.c_void_p), len(plans),
+                                _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+class Batch:
+    """rklt_batch: a graph-captured, autotuned batch over fixed device buffers."""
+
+    def __init__(self, items, plans, sse, psnr, autotune=True):
+        self._plans = list(plans)   # keep plans alive for the batch's lifetime
+        self._items = items
+        h = ctypes.c_void_p()
+        _check(lib.rklt_batch_create(ctypes.cast(items, ctypes.c_void_p), len(items),
+                                     ctypes.cast(_plan_array(self._plans), ctypes.c_void_p), len(self._plans),
+                                     _ptr(sse), _ptr(psnr), 1 if autotune else 0, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib.rklt_batch_run(self._h, _stream(stream)))
+
+    def info(self):
+        t, c, g, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib.rklt_batch_info(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g), ctypes.byref(us)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "groups": g.value, "tuned_us": us.value}
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.rklt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rklt_batch_create(items, plans, sse, psnr, autotune=True) -> Batch:
+    return Batch(items, plans, sse, psnr, autotune)
+
+
+def rklt_rsweep(plans, imgs, sse, psnr, stream=None):
+    """imgs: uint8 tensor [nimg, H, W]; psnr (and sse, or None): [nimg, nplans, N*N]."""
+    assert imgs.dim() == 3 and imgs.stride(2) == 1
+    nimg, H, W = imgs.shape
+    _check(lib.rklt_rsweep(ctypes.cast(_plan_array(plans), ctypes.c_void_p), len(plans), imgs.data_ptr(), nimg, H, W,
+                           imgs.stride(1), imgs.stride(0), _ptr(sse), _ptr(psnr), _stream(stream)))
 
 
 def rklt_device_status():

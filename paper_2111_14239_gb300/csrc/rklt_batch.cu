@@ -1,0 +1,378 @@
+// rklt_batch.cu -- many images of uneven sizes (and their own r) in one launch.
+//
+// Work is a flattened queue of "units": 32 horizontally adjacent N x N blocks of
+// one block-row of one image.  Each warp takes units round-robin; lane l owns
+// block 32u + l and runs the same per-block computation as the fused kernel
+// (block_core: exact column/row pass, zonal mask, inverse, error, 8-bit output)
+// straight from and to global memory with coalesced 8-byte row accesses (a
+// warp's 32 blocks are 256 contiguous bytes per row).  D = diag_bound(N, r) is
+// per image and selects a register-resident variant of block_core.  The SSE of
+// a unit goes to a fixed slot, and a per-image kernel sums an image's slots in
+// order, so results do not depend on the rest of the batch.
+//
+// rklt_fused_items launches immediately (continuous batching of requests);
+// rklt_batch_* builds the queue once, captures the launches in a CUDA graph
+// and picks the launch shape with a small autotuner (timed candidates).
+#include <algorithm>
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "rklt_fused_impl.cuh"
+
+namespace rklt {
+
+struct BatchItem {
+    const uint8_t *img;
+    uint8_t *recon;
+    float *zcoef;
+    int64_t ld, ld_recon;
+    int64_t unit_base;  // first unit of this item in the queue
+    int H, W, r, D;
+    int bw, units_x;    // blocks per block-row, units per block-row
+    int vec4;           // coefficients as float4 (r % 4 == 0, 16-byte aligned)
+    int out_index;      // position of this item in the caller's d_sse / d_psnr
+};
+
+template <int N, int D>
+__global__ void __launch_bounds__(256, 1)
+    batch_kernel(const __grid_constant__ PlanK<N> P, const BatchItem *__restrict__ items, int nitems, int64_t nunits,
+                 float *__restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t u = warp0; u < nunits; u += nwarps) {
+        int lo = 0, hi = nitems - 1;  // last item with unit_base <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].unit_base <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItem it = items[lo];
+        const int64_t local = u - it.unit_base;
+        const int by = int(local / it.units_x);
+        const int bx = int(local - int64_t(by) * it.units_x) * 32 + lane;
+        float sse = 0.0f;
+        if (bx < it.bw) {
+            uint32_t w[N][N / 4];
+            load_block_words<N>(it.img + int64_t(by) * N * it.ld + bx * N, it.ld, w);
+            uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
+            float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
+            sse = block_core<N, D>(P, w, dst, it.ld_recon, it.r, coef, it.vec4 != 0, dst != nullptr);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
+        if (lane == 0) partials[u] = sse;
+    }
+}
+
+// One CTA per item: FP64 sum of its unit partials in order, then PSNR.
+__global__ void batch_finalize(const BatchItem *__restrict__ items, int nitems, int64_t nunits,
+                               const float *__restrict__ partials, double *sse, float *psnr) {
+    __shared__ double red[256];
+    const int i = blockIdx.x;
+    if (i >= nitems) return;
+    const BatchItem it = items[i];
+    const int64_t end = (i + 1 < nitems) ? items[i + 1].unit_base : nunits;
+    double acc = 0.0;
+    for (int64_t u = it.unit_base + threadIdx.x; u < end; u += blockDim.x) acc += double(partials[u]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double s = red[0], npx = double(it.H) * double(it.W);
+        sse[it.out_index] = s;
+        float p;
+        if (npx == 0.0) p = __int_as_float(0x7fc00000);
+        else if (s == 0.0) p = __int_as_float(0x7f800000);
+        else p = float(10.0 * log10(255.0 * 255.0 * npx / s));
+        psnr[it.out_index] = p;
+    }
+}
+
+namespace {
+
+struct Group {
+    const Plan *plan = nullptr;
+    int D = 0;  // every item of a group has the same retained support
+    std::vector<BatchItem> items;
+    int64_t nunits = 0;
+};
+
+// Validate items and split them by plan, building each group's unit queue.
+rklt_status build_groups(const rklt_item *h, int n, const rklt_plan *const *plans, int nplans, std::vector<Group> &out,
+                         int &N) {
+    if (n < 1 || !h) return fail(RKLT_ERR_ARG, "need at least one item");
+    if (nplans < 1 || !plans) return fail(RKLT_ERR_ARG, "need at least one plan");
+    N = 0;
+    for (int p = 0; p < nplans; p++) {
+        if (!plans[p]) return fail(RKLT_ERR_ARG, "NULL plan");
+        if (N == 0) N = plans[p]->p.N;
+        if (plans[p]->p.N != N) return fail(RKLT_ERR_ARG, "all plans of a batch must share N");
+    }
+    if (N != 4 && N != 8) return fail(RKLT_ERR_UNSUPPORTED, "batched launches support N = 4 and N = 8");
+    const uintptr_t amask = N == 8 ? 7 : 3;
+    std::map<std::pair<int, int>, int> gidx;
+    out.clear();
+    for (int i = 0; i < n; i++) {
+        const rklt_item &x = h[i];
+        if (x.plan < 0 || x.plan >= nplans) return fail(RKLT_ERR_ARG, "item plan index out of range");
+        if (x.r < 0 || x.r > N * N) return fail(RKLT_ERR_ARG, "item r must lie in [0, N*N]");
+        if (x.H < 0 || x.W < 0 || x.H % N || x.W % N)
+            return fail(RKLT_ERR_SHAPE, "item H and W must be non-negative multiples of N");
+        if (x.ld < x.W) return fail(RKLT_ERR_SHAPE, "item ld must be >= W");
+        if (x.H > 0 && x.W > 0 && !x.d_img) return fail(RKLT_ERR_ARG, "item image is NULL");
+        if ((reinterpret_cast<uintptr_t>(x.d_img) | uintptr_t(x.ld)) & amask)
+            return fail(RKLT_ERR_UNSUPPORTED, "batched items need N-byte aligned image rows");
+        if (x.d_recon) {
+            if (x.ld_recon < x.W) return fail(RKLT_ERR_SHAPE, "item ld_recon must be >= W");
+            if ((reinterpret_cast<uintptr_t>(x.d_recon) | uintptr_t(x.ld_recon)) & amask)
+                return fail(RKLT_ERR_UNSUPPORTED, "batched items need N-byte aligned reconstruction rows");
+        }
+        if (x.d_zcoef && (reinterpret_cast<uintptr_t>(x.d_zcoef) & 3))
+            return fail(RKLT_ERR_ARG, "item coefficient pointer must be 4-byte aligned");
+        const int D = diag_bound(N, x.r);
+        auto f = gidx.find({x.plan, D});
+        if (f == gidx.end()) {
+            f = gidx.emplace(std::make_pair(x.plan, D), int(out.size())).first;
+            out.emplace_back();
+            out.back().plan = &plans[x.plan]->p;
+            out.back().D = D;
+        }
+        Group &g = out[f->second];
+        BatchItem b{};
+        b.img = x.d_img;
+        b.recon = x.d_recon;
+        b.zcoef = x.d_zcoef;
+        b.ld = x.ld;
+        b.ld_recon = x.ld_recon;
+        b.H = x.H;
+        b.W = x.W;
+        b.r = x.r;
+        b.D = D;
+        b.bw = x.W / N;
+        b.units_x = (b.bw + 31) / 32;
+        b.vec4 = (x.r % 4 == 0) && ((reinterpret_cast<uintptr_t>(x.d_zcoef) & 15) == 0);
+        b.out_index = i;
+        b.unit_base = g.nunits;
+        g.nunits += int64_t(x.H / N) * b.units_x;
+        g.items.push_back(b);
+    }
+    return RKLT_OK;
+}
+
+template <int N, int D>
+const void *batch_fn() { return reinterpret_cast<const void *>(batch_kernel<N, D>); }
+
+// Host-side table of the batch kernels, indexed by D.
+template <int N, int... Ds>
+const void *pick_fn(int D, std::integer_sequence<int, Ds...>) {
+    const void *tab[] = {batch_fn<N, Ds>()...};
+    return tab[D];
+}
+
+const void *batch_kernel_for(int N, int D) {
+    return N == 4 ? pick_fn<4>(D, std::make_integer_sequence<int, 8>{})
+                  : pick_fn<8>(D, std::make_integer_sequence<int, 16>{});
+}
+
+cudaError_t launch_group(int N, const Group &g, const BatchItem *d_items, float *partials, double *sse, float *psnr,
+                         int threads, int grid, cudaStream_t st) {
+    const int nitems = int(g.items.size());
+    int64_t nunits = g.nunits;
+    if (nunits > 0) {
+        const void *fn = batch_kernel_for(N, g.D);
+        const void *kp = g.plan->k.data();
+        void *args[] = {const_cast<void *>(kp), &d_items, const_cast<int *>(&nitems), &nunits, &partials};
+        const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    batch_finalize<<<nitems, 256, 0, st>>>(d_items, nitems, nunits, partials, sse, psnr);
+    return cudaGetLastError();
+}
+
+// Largest useful persistent grid for `threads` per CTA and `per_sm` CTAs per SM.
+int grid_for(int N, int threads, int per_sm, int64_t nunits) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_for(N, N == 4 ? 7 : 15), threads, 0);
+    const int use = std::max(1, std::min(per_sm, occ));
+    const int64_t warps_needed = nunits;
+    const int64_t ctas_needed = (warps_needed * 32 + threads - 1) / threads;
+    return int(std::max<int64_t>(1, std::min<int64_t>(int64_t(use) * sm_count(dev), ctas_needed)));
+}
+
+}  // namespace
+}  // namespace rklt
+
+struct rklt_batch {
+    int N = 0;
+    std::vector<rklt::Group> groups;
+    std::vector<rklt::BatchItem *> d_items;
+    std::vector<float *> d_partials;
+    double *sse = nullptr;
+    float *psnr = nullptr;
+    int threads = 256, per_sm = 1;
+    double tuned_us = 0.0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+using namespace rklt;
+
+namespace {
+
+void batch_free(rklt_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto p : b->d_items) cudaFree(p);
+    for (auto p : b->d_partials) cudaFree(p);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+cudaError_t batch_enqueue(rklt_batch *b, int threads, int per_sm, cudaStream_t st) {
+    for (size_t gi = 0; gi < b->groups.size(); gi++) {
+        const Group &g = b->groups[gi];
+        const int grid = grid_for(b->N, threads, per_sm, g.nunits);
+        const cudaError_t e =
+            launch_group(b->N, g, b->d_items[gi], b->d_partials[gi], b->sse, b->psnr, threads, grid, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,
+                             double *d_sse, float *d_psnr, void *stream) {
+    std::vector<Group> groups;
+    int N = 0;
+    rklt_status s = build_groups(h_items, n, plans, nplans, groups, N);
+    if (s != RKLT_OK) return s;
+    if (!d_sse || !d_psnr) return fail(RKLT_ERR_ARG, "d_sse and d_psnr are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool) return fail(RKLT_ERR_CUDA, "could not create the scratch memory pool");
+    for (const Group &g : groups) {
+        const size_t ib = g.items.size() * sizeof(BatchItem);
+        const size_t pb = size_t(std::max<int64_t>(g.nunits, 1)) * sizeof(float);
+        void *scratch = nullptr;
+        if (cudaMallocFromPoolAsync(&scratch, ib + pb, pool, st) != cudaSuccess)
+            return fail(RKLT_ERR_OOM, "scratch allocation failed");
+        BatchItem *d_items = static_cast<BatchItem *>(scratch);
+        float *partials = reinterpret_cast<float *>(static_cast<char *>(scratch) + ib);
+        // pageable source: the runtime stages it before returning, so g.items may go away
+        cudaError_t e = cudaMemcpyAsync(d_items, g.items.data(), ib, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = launch_group(N, g, d_items, partials, d_sse, d_psnr, 256, grid_for(N, 256, 1, g.nunits), st);
+        cudaFreeAsync(scratch, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    }
+    return RKLT_OK;
+}
+
+rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,
+                              double *d_sse, float *d_psnr, int flags, rklt_batch **out) {
+    if (!out) return fail(RKLT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d_sse || !d_psnr) return fail(RKLT_ERR_ARG, "d_sse and d_psnr are required");
+    rklt_batch *b = new (std::nothrow) rklt_batch;
+    if (!b) return fail(RKLT_ERR_OOM, "host allocation failed");
+    rklt_status s = build_groups(h_items, n, plans, nplans, b->groups, b->N);
+    if (s != RKLT_OK) {
+        delete b;
+        return s;
+    }
+    b->sse = d_sse;
+    b->psnr = d_psnr;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    for (const Group &g : b->groups) {
+        if (e != cudaSuccess) break;
+        BatchItem *di = nullptr;
+        float *dp = nullptr;
+        e = cudaMalloc(&di, g.items.size() * sizeof(BatchItem));
+        if (e == cudaSuccess) e = cudaMalloc(&dp, size_t(std::max<int64_t>(g.nunits, 1)) * sizeof(float));
+        b->d_items.push_back(di);
+        b->d_partials.push_back(dp);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(di, g.items.data(), g.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return e == cudaErrorMemoryAllocation ? fail(RKLT_ERR_OOM, "device allocation for the batch failed")
+                                              : cuda_fail(e, "batch set-up");
+    }
+    // autotuner: time each launch shape twice on the batch's own data and keep the fastest
+    struct Cand {
+        int threads, per_sm;
+    };
+    std::vector<Cand> cands = {{256, 1}, {128, 2}, {128, 1}, {256, 2}};
+    if (!(flags & 1)) cands.resize(1);
+    double best = 1e30;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (const Cand &c : cands) {
+        if (batch_enqueue(b, c.threads, c.per_sm, b->stream) != cudaSuccess) continue;  // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int rep = 0; rep < 2; rep++) batch_enqueue(b, c.threads, c.per_sm, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / 2 < best) {
+            best = ms / 2;
+            b->threads = c.threads;
+            b->per_sm = c.per_sm;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned_us = (flags & 1) ? best * 1e3 : 0.0;
+    // capture the chosen launch sequence once; runs replay the graph
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t le = batch_enqueue(b, b->threads, b->per_sm, b->stream);
+        e = cudaStreamEndCapture(b->stream, &b->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch graph capture");
+    }
+    *out = b;
+    return RKLT_OK;
+}
+
+rklt_status rklt_batch_run(rklt_batch *b, void *stream) {
+    if (!b) return fail(RKLT_ERR_ARG, "batch is NULL");
+    const cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RKLT_OK : cuda_fail(e, "graph launch");
+}
+
+rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us) {
+    if (!b) return fail(RKLT_ERR_ARG, "batch is NULL");
+    if (threads) *threads = b->threads;
+    if (ctas_per_sm) *ctas_per_sm = b->per_sm;
+    if (groups) *groups = int(b->groups.size());
+    if (tuned_us) *tuned_us = b->tuned_us;
+    return RKLT_OK;
+}
+
+void rklt_batch_destroy(rklt_batch *b) {
+    if (b && b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+}  // extern "C"

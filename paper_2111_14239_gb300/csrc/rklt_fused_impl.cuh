@@ -59,25 +59,31 @@ constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies alrea
 // run in FP32; the error takes each pixel straight from its exact half with a
 // mixed-precision subtraction.
 // ---------------------------------------------------------------------------
+// Loads the N x N block at src (row stride ld bytes) as N/4 words per row.
+template <int N>
+__device__ __forceinline__ void load_block_words(const uint8_t *src, int64_t ld, uint32_t (&w)[N][N / 4]) {
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        if constexpr (N == 8) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(src + k * ld);
+            w[k][0] = v.x;
+            w[k][1] = v.y;
+        } else {
+            w[k][0] = *reinterpret_cast<const uint32_t *>(src + k * ld);
+        }
+    }
+}
+
+// The whole per-block computation on a block held in registers (w); the 8-bit
+// reconstruction is written to dst (row stride ldd bytes) when recon is set.
 template <int N, int D>
-__device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
-                                           bool recon) {
+__device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&w)[N][N / 4], uint8_t *dst,
+                                            int64_t ldd, int r, float *coef, bool vec4, bool recon) {
     constexpr int H2 = N / 2;
     constexpr int NP = N / 2;           // column pairs
     constexpr int DR = D < N ? D : N;   // rows / columns of C that carry retained terms
     constexpr int DA = DR > 0 ? DR : 1; // array extent (D = 0 keeps nothing)
     const __half2 k1024 = __float2half2_rn(1024.0f);
-    uint32_t w[N][N / 4];  // the block's bytes, 4 pixels per word
-#pragma unroll
-    for (int k = 0; k < N; k++) {
-        if constexpr (N == 8) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(blk + k * TW);
-            w[k][0] = v.x;
-            w[k][1] = v.y;
-        } else {
-            w[k][0] = *reinterpret_cast<const uint32_t *>(blk + k * TW);
-        }
-    }
     // pixels (A[k][2p], A[k][2p+1]) of column pair p as exact binary16 pairs
     auto px = [&](int k, int p) -> __half2 {
         return __hsub2(as_h2(bytes_to_biased_h2(w[k][p >> 1], (2 * p) & 3, (2 * p + 1) & 3)), k1024);
@@ -203,15 +209,24 @@ __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int 
         }
         if (recon) {
             if constexpr (N == 8) {
-                *reinterpret_cast<uint2 *>(blk + k * TW) = make_uint2(wt[0], wt[1]);
-                *reinterpret_cast<uint2 *>(blk + (N - 1 - k) * TW) = make_uint2(wb[0], wb[1]);
+                *reinterpret_cast<uint2 *>(dst + k * ldd) = make_uint2(wt[0], wt[1]);
+                *reinterpret_cast<uint2 *>(dst + (N - 1 - k) * ldd) = make_uint2(wb[0], wb[1]);
             } else {
-                *reinterpret_cast<uint32_t *>(blk + k * TW) = wt[0];
-                *reinterpret_cast<uint32_t *>(blk + (N - 1 - k) * TW) = wb[0];
+                *reinterpret_cast<uint32_t *>(dst + k * ldd) = wt[0];
+                *reinterpret_cast<uint32_t *>(dst + (N - 1 - k) * ldd) = wb[0];
             }
         }
     }
     return sse2.x + sse2.y;
+}
+
+// One block of a shared-memory tile, transformed in place.
+template <int N, int D>
+__device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
+                                           bool recon) {
+    uint32_t w[N][N / 4];
+    load_block_words<N>(blk, TW, w);
+    return block_core<N, D>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
 template <int N>

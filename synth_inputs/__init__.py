@@ -172,3 +172,41 @@ def serving_requests(rate_hz: float, duration_s: float, seed: int = 5000,
         out.append((t, h, w, rho, r, seed + 1 + i))
         i += 1
     return out
+
+
+# --------------------------------------------------------------------------
+# Large pools by cropping: a window of an AR(1) field is itself an AR(1) field
+# with the same rho, so many distinct images of any size come from a few large
+# base fields (one per rho) without drawing each one from scratch.
+# --------------------------------------------------------------------------
+
+def base_fields(rhos, side: int = 4096, base_seed: int = 6000) -> dict:
+    """{rho: uint8 side x side AR(1) image}, seed base_seed + index of rho."""
+    return {float(rho): ar1_image(side, side, float(rho), base_seed + k) for k, rho in enumerate(rhos)}
+
+
+def crop(base: np.ndarray, h: int, w: int, seed: int) -> np.ndarray:
+    """h x w window of `base` at an offset drawn from PCG64(seed) (requires h, w <= side)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    y = int(g.integers(0, base.shape[0] - h + 1))
+    x = int(g.integers(0, base.shape[1] - w + 1))
+    return base[y:y + h, x:x + w]
+
+
+def mixed_batch(items: list, bases: dict) -> list:
+    """Images for mixed_items(): each a crop of the base field whose rho is the
+    grid value nearest to the item's rho."""
+    return [crop(bases[nearest_grid_rho(it.rho, tuple(bases))], it.h, it.w, it.seed) for it in items]
+
+
+def serving_pool(n: int, bases: dict, median: float = 768.0, sigma: float = 0.5, seed: int = 5100) -> list:
+    """n request images with lognormal sides (median, sigma; multiples of 8 in
+    [64, 4096]) cropped from the base fields, rho cycling over the bases."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    keys = list(bases)
+    out = []
+    for i in range(n):
+        h = lognormal_side(g, median, sigma)
+        w = lognormal_side(g, median, sigma)
+        out.append(crop(bases[keys[i % len(keys)]], h, w, seed + 1 + i))
+    return out

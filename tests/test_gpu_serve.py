@@ -1,0 +1,68 @@
+"""Serving loop: continuous batching over a Poisson trace; every result must be the
+same as the request computed alone, and match the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import synth_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RHOS = (0.5, 0.8, 0.9, 0.95)
+
+
+@pytest.fixture(scope="module")
+def serve():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2111_14239_gb300 import serve
+    return serve
+
+
+def _pool(n=12, seed=77):
+    g = np.random.Generator(np.random.PCG64(seed))
+    return [si.ar1_image(si.lognormal_side(g, median=192, lo=8, hi=512),
+                         si.lognormal_side(g, median=192, lo=8, hi=512), 0.9, 4000 + i) for i in range(n)]
+
+
+def test_continuous_batching_results_equal_alone(serve, orc):
+    import paper_2111_14239_gb300 as rk
+    pool = _pool()
+    trace = serve.make_trace(800.0, 0.3, pool, seed=3)
+    srv = serve.Server(RHOS, budget_bytes=64 << 20, streams=3)
+    stats = srv.run(trace, keep_outputs=True)
+    assert stats["requests"] == len(trace) and stats["rejected"] == 0
+    assert all(r.done >= r.arrival for r in trace)
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    # alone: one request per launch on fresh buffers gives bit-identical results
+    for req in trace[:: max(1, len(trace) // 12)]:
+        h, w = req.image.shape
+        d = torch.from_numpy(req.image).cuda()
+        rec = torch.zeros_like(d)
+        zc = torch.zeros((h // 8) * (w // 8) * req.r, device="cuda")
+        s = torch.zeros(1, dtype=torch.float64, device="cuda")
+        p = torch.zeros(1, dtype=torch.float32, device="cuda")
+        rk.rklt_fused_items(rk.make_items([(d, req.plan, req.r, zc, rec)]), srv.plans, s, p)
+        torch.cuda.synchronize()
+        assert s.item() == req.sse and p.item() == req.psnr
+        assert np.array_equal(rec.cpu().numpy(), req.recon)
+        assert np.array_equal(zc.cpu().numpy(), req.coef)
+        op = orc.Plan(8, RHOS[req.plan])
+        sref, _, _ = orc.pipeline(8, op.That, req.image, req.r)
+        if sref > 0 and 10 * math.log10(255 ** 2 * req.image.size / sref) < 60:
+            assert abs(req.sse - sref) <= 2.3e-4 * sref
+
+
+def test_budget_admission(serve):
+    pool = _pool(6, seed=5)
+    big = si.ar1_image(2048, 2048, 0.9, 1)     # needs more than the budget below
+    trace = serve.make_trace(400.0, 0.1, pool + [big], seed=9)
+    need_big = sum(serve._align(b) for b in serve.bytes_needed(2048, 2048, 64))
+    srv = serve.Server(RHOS, budget_bytes=need_big // 2, streams=2)
+    stats = srv.run(trace)
+    n_big = sum(1 for r in trace if r.image is big and sum(serve._align(b) for b in serve.bytes_needed(
+        2048, 2048, r.r)) > need_big // 2)
+    assert stats["rejected"] == n_big
+    assert all(not math.isnan(r.psnr) for r in trace if r.image is not big)
