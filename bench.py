@@ -106,9 +106,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_images():
+def make_images(rank: int = 0):
+    """This rank's 16 images: seeds 2000 + 16*rank + i (rank 0 = the single-GPU workload)."""
     import synth_inputs as si
-    return si.roofline_batch(NIMG, SIDE, 2000)
+    from paper_2111_14239_gb300 import replicas
+    return si.roofline_batch(NIMG, SIDE, replicas.image_seeds(2000, NIMG, rank)[0])
 
 
 # ---------------------------------------------------------------------------
@@ -182,7 +184,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    imgs_np = make_images()
+    imgs_np = make_images(rank)
     H = W = SIDE
     plans = {n: rk.rklt_make(n, RHO) for n in NS}
     rs = {n: n * n // 8 for n in NS}
@@ -230,14 +232,12 @@ def run_ours(args):
         dist.barrier()
     ms = start.elapsed_time(stop)
     kern_ms = {n: statistics.mean(e[n][0].elapsed_time(e[n][1]) for e in evs) for n in NS}
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2111_14239_gb300 import replicas
+    ms = replicas.max_over_ranks(ms, dev)
     rk.rklt_device_status()
 
     px_step = len(NS) * NIMG * H * W
-    value = px_step * args.steps * world / (ms / 1e3) / 1e6
+    value = replicas.job_throughput(px_step * args.steps, world, ms / 1e3) / 1e6
 
     # ---- end to end through the C ABI with host buffers
     pin_in = torch.from_numpy(imgs_np).pin_memory()
@@ -265,11 +265,7 @@ def run_ours(args):
         e2e_step()
     t2.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = s2.elapsed_time(t2)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(s2.elapsed_time(t2), dev)
     h2d = imgs_np.nbytes
     d2h = sum(pin_out[n]["zc"].numel() * 4 + pin_out[n]["rec"].numel() + NIMG * 4 for n in NS)
     e2e_val = px_step * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None

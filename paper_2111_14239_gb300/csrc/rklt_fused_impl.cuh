@@ -436,7 +436,7 @@ template <int N>
 __host__ __device__ constexpr int coop2_rounds() { return TH / N; }
 
 __host__ __device__ inline bool coop2_stage_coef(int N, int r) {
-    return int64_t(TH / N) * (TW / N) * r * 4 <= 32 * 1024;
+    return int64_t(TH / N) * (TW / N) * (r | 1) * 4 <= 32 * 1024;
 }
 
 template <int N, int DRM>
@@ -514,7 +514,7 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
         for (int l = 0; l < H2; l++) xe[l] = xo[l] = 0.0f;
         const int jmax = D - i;
         const float si = P.s[i];
-        float *zs = Zs + (round * NB + b) * r;
+        float *zs = Zs + (round * NB + b) * (r | 1);  // odd block stride: no bank conflicts
         float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
                                          int64_t(tc.ty * R + round) * bw + tc.tx * NB + b) * r
                             : nullptr;
@@ -557,8 +557,11 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
         for (int round = 0; round < rows_in; round++) {
             float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * R + round) * bw +
                                     tc.tx * NB) * r;
-            const float *src = Zs + round * NB * r;
-            for (int q = ct; q < nb_in * r; q += NCONS) dst[q] = src[q];
+            const float *src = Zs + round * NB * (r | 1);
+            for (int q = ct; q < nb_in * r; q += NCONS) {
+                const int bq = q / r;
+                dst[q] = src[bq * (r | 1) + (q - bq * r)];
+            }
         }
     }
 
@@ -614,19 +617,28 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
     return sse;
 }
 
-template <int N>
+// Kernel variant V (picked on the host from the diagonal bound D):
+//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), 1 cooperative;
+//   N >= 16: 1, 2, 3 = cooperative path sized for Dr <= N/4, N/2, N.
+__host__ __device__ inline int fused_variant(int N, int D) {
+    if (N == 4) return 0;
+    if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
+    const int Dr = D < N ? D : N;
+    return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
+}
+
+template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
                                               int ct, float *Ys, float *Zs) {
     if constexpr (N == 4) {
         return tile_reg<4>(P, g, tile, tile_id, ct);
     } else if constexpr (N == 8) {
-        if (g.D <= REG_DMAX8) return tile_reg<8>(P, g, tile, tile_id, ct);
-        return tile_coop<8>(P, g, tile, tile_id, ct, Ys, Zs);
+        if constexpr (V == 0) return tile_reg<8>(P, g, tile, tile_id, ct);
+        else return tile_coop<8>(P, g, tile, tile_id, ct, Ys, Zs);
     } else {
-        const int Dr = g.D < N ? g.D : N;
-        if (Dr <= N / 4) return tile_coop2<N, N / 4>(P, g, tile, tile_id, ct, Ys, Zs);
-        if (Dr <= N / 2) return tile_coop2<N, N / 2>(P, g, tile, tile_id, ct, Ys, Zs);
-        return tile_coop2<N, N>(P, g, tile, tile_id, ct, Ys, Zs);
+        if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tile_id, ct, Ys, Zs);
+        else if constexpr (V == 2) return tile_coop2<N, N / 2>(P, g, tile, tile_id, ct, Ys, Zs);
+        else return tile_coop2<N, N>(P, g, tile, tile_id, ct, Ys, Zs);
     }
 }
 
@@ -675,7 +687,7 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
     if (N >= 16) {
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
-        zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * r * 4 : 0;
+        zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
     } else if (N == 8 && D > REG_DMAX8) {
         ys = N * LDY * 4;
         zs = (TW / N) * r * 4;
@@ -688,7 +700,7 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
 // ---------------------------------------------------------------------------
 // The kernel: warps 0..7 consume; warp 8 produces in TMA mode (idle otherwise).
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(NCONS + 32, 2)
     fused_kernel(const __grid_constant__ PlanK<N> P, const __grid_constant__ CUtensorMap tm_in,
                  const __grid_constant__ CUtensorMap tm_out, const FusedGeom g) {
@@ -771,7 +783,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    const bool coop = (N >= 16) || (N == 8 && g.D > REG_DMAX8);
+    constexpr bool coop = (N >= 16) || (N == 8 && V == 1);
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
         uint8_t *buf;
@@ -811,7 +823,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             }
             named_sync(1, NCONS);
         }
-        float v = process_tile<N>(P, g, buf, tile, tid, Ys, Zs);
+        float v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
         if (g.use_tma) {
             // warp partial -> red[s][warp]; the producer sums the eight in order
 #pragma unroll
@@ -933,12 +945,28 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     g.use_tma = tma ? 1 : 0;
     g.stages = (N >= 16) ? 3 : STAGES;
     const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D);
-    const int dev = ensure_smem_attr(reinterpret_cast<const void *>(fused_kernel<N>));
+    const int V = fused_variant(N, g.D);
+    const void *fn = nullptr;
+    if constexpr (N == 4) fn = reinterpret_cast<const void *>(fused_kernel<4, 0>);
+    else if constexpr (N == 8) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<8, 0>)
+                                           : reinterpret_cast<const void *>(fused_kernel<8, 1>);
+    else fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
+                     : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
+                               : reinterpret_cast<const void *>(fused_kernel<N, 3>));
+    const int dev = ensure_smem_attr(fn);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<N>, NCONS + 32, L.total);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NCONS + 32, L.total);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(g.ntiles, int64_t(per_sm) * sm_count(dev));
-    fused_kernel<N><<<unsigned(grid), NCONS + 32, L.total, st>>>(plan.kparams<N>(), tin, tout, g);
+    {
+        const PlanK<N> &pk = plan.kparams<N>();
+        void *args[] = {const_cast<PlanK<N> *>(&pk), &tin, &tout, &g};
+        const cudaError_t le = cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(NCONS + 32), args, L.total, st);
+        if (le != cudaSuccess) {
+            if (scratch) cudaFreeAsync(scratch, st);
+            return cuda_fail(le, "fused kernel launch");
+        }
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
         finalize_kernel<<<a.nimg, 256, 0, st>>>(g.partials, tiles_per_img, a.nimg, a.H, a.W, a.sse, a.psnr);
