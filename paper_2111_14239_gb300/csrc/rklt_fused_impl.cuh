@@ -480,13 +480,15 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
 #pragma unroll
         for (int i = 0; i < DRM; i++) {
             if (i < Dr) {
-                float2 acc = make_float2(0.0f, 0.0f);
+                // scalar FFMA: T's entries stay constant-bank operands
+                float ax = 0.0f, ay = 0.0f;
 #pragma unroll
                 for (int j = 0; j < H2; j++) {
-                    const float tv = P.T[i][j];
-                    acc = __ffma2_rn(make_float2(tv, tv), (i & 1) ? dp[j] : sp[j], acc);
+                    const float2 v = (i & 1) ? dp[j] : sp[j];
+                    ax = fmaf(P.T[i][j], v.x, ax);
+                    ay = fmaf(P.T[i][j], v.y, ay);
                 }
-                *reinterpret_cast<float2 *>(dst + i * NB * LB) = acc;
+                *reinterpret_cast<float2 *>(dst + i * NB * LB) = make_float2(ax, ay);
             }
         }
     }
@@ -518,8 +520,10 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
         float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
                                          int64_t(tc.ty * R + round) * bw + tc.tx * NB + b) * r
                             : nullptr;
+        // D <= DRM in every variant but the last, so C[i][j] != 0 only for j < min(DRM, N)
+        constexpr int JM = DRM < N ? DRM : N;
 #pragma unroll
-        for (int j = 0; j < N; j++) {
+        for (int j = 0; j < JM; j++) {
             if (j < jmax) {
                 float acc = 0.0f;
 #pragma unroll
@@ -583,15 +587,20 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
         float2 sse2 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int k = 0; k < H2; k++) {
-            float2 e2 = make_float2(0.0f, 0.0f), o2 = make_float2(0.0f, 0.0f);
+            float ex = 0.0f, ey = 0.0f, ox = 0.0f, oy = 0.0f;
 #pragma unroll
             for (int i = 0; i < DRM; i++) {
                 if (i < Dr) {
-                    const float tv = P.Ti[k][i];
-                    if (i & 1) o2 = __ffma2_rn(make_float2(tv, tv), xv[i], o2);
-                    else e2 = __ffma2_rn(make_float2(tv, tv), xv[i], e2);
+                    if (i & 1) {
+                        ox = fmaf(P.Ti[k][i], xv[i].x, ox);
+                        oy = fmaf(P.Ti[k][i], xv[i].y, oy);
+                    } else {
+                        ex = fmaf(P.Ti[k][i], xv[i].x, ex);
+                        ey = fmaf(P.Ti[k][i], xv[i].y, ey);
+                    }
                 }
             }
+            const float2 e2 = make_float2(ex, ey), o2 = make_float2(ox, oy);
             const float2 top = __fadd2_rn(e2, o2), bot = __ffma2_rn(o2, neg1, e2);
             uint16_t *pt = reinterpret_cast<uint16_t *>(col + k * TW);
             uint16_t *pb = reinterpret_cast<uint16_t *>(col + (N - 1 - k) * TW);
