@@ -15,7 +15,7 @@
 // formed, and only their inverse contributions are summed.
 //
 // Data movement: the image is cut into 64-row x 256-byte tiles.  When pointers
-// and pitches are 16-byte aligned a producer warp streams tiles into a 4-stage
+// and pitches are 16-byte aligned a producer warp streams tiles into a 3- to 6-stage
 // shared-memory ring with 3-D TMA bulk tensor copies (mbarrier completion), the
 // eight consumer warps transform them in place, and the producer writes the
 // rounded 8-bit reconstruction back with TMA bulk tensor stores.  Otherwise the
@@ -24,9 +24,13 @@
 //
 // Work split inside a tile:
 //   register path  (N = 4, and N = 8 with D <= 5): one thread owns a whole block;
-//   cooperative path (N = 16, 32, and N = 8 with D > 5): per block-row of the
-//     tile, threads own columns for the column passes and (block, row) pairs for
-//     the row passes, exchanging through a padded shared-memory buffer.
+//   tensor-core path (N = 32 with D <= 16, rklt_tc.cuh): one warp owns a block and
+//     runs every contraction as fp16 mma.sync; tiles then arrive as two 128-byte
+//     swizzled halves;
+//   cooperative path (N = 16, N = 32 with D > 16, and N = 8 with D > 5): per
+//     block-row of the tile, threads own columns for the column passes and
+//     (block, row) pairs for the row passes, exchanging through a padded
+//     shared-memory buffer.
 #pragma once
 
 #include <cudaTypedefs.h>
@@ -42,7 +46,7 @@ namespace rklt {
 constexpr int TW = 256;          // tile width in bytes (pixels)
 constexpr int TH = 64;           // tile height in rows
 constexpr int TILE_BYTES = TW * TH;
-constexpr int STAGES = 4;        // TMA ring depth
+constexpr int STAGES = 8;        // deepest TMA ring (barrier and reduction slots)
 constexpr int NCONS = 256;       // consumer threads (8 warps); one producer warp follows
 constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchange buffer (floats)
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
@@ -626,12 +630,20 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
     return sse;
 }
 
+}  // namespace rklt
+
+#include "rklt_tc.cuh"
+
+namespace rklt {
+
 // Kernel variant V (picked on the host from the diagonal bound D):
 //   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), 1 cooperative;
-//   N >= 16: 1, 2, 3 = cooperative path sized for Dr <= N/4, N/2, N.
+//   N = 32 with D <= 16: TC_V (tensor cores, one warp per block);
+//   N >= 16 otherwise: 1, 2, 3 = cooperative path sized for Dr <= N/4, N/2, N.
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
     if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
+    if (N == 32 && D <= TC_DMAX) return TC_V;
     const int Dr = D < N ? D : N;
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
@@ -681,6 +693,39 @@ __device__ __forceinline__ void tile_origin(const FusedGeom &g, int64_t tile_id,
     x = t.tx * TW;
 }
 
+// Tile layout in shared memory: row-major 64 x 256 bytes, or (tensor-core variant)
+// two 64 x 128 halves in the 128-byte swizzled layout.
+template <int V>
+__device__ __forceinline__ int tile_off(int y, int x) {
+    if constexpr (V == TC_V) return swz_off(y, x);
+    else return y * TW + x;
+}
+
+// TMA copies of one tile: one 256 x 64 box, or two 128 x 64 swizzled boxes (the
+// second only when it starts inside the image).
+template <int V>
+__device__ __forceinline__ void load_tile(const CUtensorMap *map, const FusedGeom &g, int x, int y, int z,
+                                          uint8_t *dst, uint64_t *bar) {
+    if constexpr (V == TC_V) {
+        const bool two = x + TW / 2 < g.W;
+        mbar_arrive_expect_tx(bar, two ? TILE_BYTES : TC_HALF);
+        tma_load_3d(dst, map, x, y, z, bar);
+        if (two) tma_load_3d(dst + TC_HALF, map, x + TW / 2, y, z, bar);
+    } else {
+        mbar_arrive_expect_tx(bar, TILE_BYTES);
+        tma_load_3d(dst, map, x, y, z, bar);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_tile(const CUtensorMap *map, const FusedGeom &g, int x, int y, int z,
+                                           const uint8_t *src) {
+    tma_store_3d(map, x, y, z, src);
+    if constexpr (V == TC_V) {
+        if (x + TW / 2 < g.W) tma_store_3d(map, x + TW / 2, y, z, src + TC_HALF);
+    }
+}
+
 // Shared memory after 1 KB alignment: tile ring | barriers | reduction | Ys | Zs.
 struct SmemLayout {
     int bar_off, red_off, ys_off, zs_off, total;
@@ -693,7 +738,9 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
     L.red_off = L.bar_off + 2 * STAGES * 8;
     L.ys_off = L.red_off + STAGES * (NCONS / 32) * 4;  // barrier and reduction slots for the deepest ring
     int ys = 0, zs = 0;
-    if (N >= 16) {
+    if (fused_variant(N, D) == TC_V) {
+        zs = (NCONS / 32) * TC_ZS * 4 + TC_TAB_BYTES;
+    } else if (N >= 16) {
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
@@ -751,7 +798,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                 if (g.recon) {
                     int x, y, z;
                     tile_origin(g, prev, x, y, z);
-                    tma_store_3d(&tm_out, x, y, z, smem + s * TILE_BYTES);
+                    store_tile<V>(&tm_out, g, x, y, z, smem + s * TILE_BYTES);
                     bulk_commit();
                     bulk_wait_read_all();  // the store has read the slot before it is refilled
                 }
@@ -759,8 +806,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             if (g.inject_stall) continue;  // test hook: nothing ever completes full[s]
             int x, y, z;
             tile_origin(g, tile, x, y, z);
-            mbar_arrive_expect_tx(&full[s], TILE_BYTES);
-            tma_load_3d(smem + s * TILE_BYTES, &tm_in, x, y, z, &full[s]);
+            load_tile<V>(&tm_in, g, x, y, z, smem + s * TILE_BYTES, &full[s]);
         }
         // drain: write back the slots still holding consumed tiles
         const int64_t issued = it;
@@ -778,7 +824,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             if (g.recon) {
                 int x, y, z;
                 tile_origin(g, tj, x, y, z);
-                tma_store_3d(&tm_out, x, y, z, smem + s * TILE_BYTES);
+                store_tile<V>(&tm_out, g, x, y, z, smem + s * TILE_BYTES);
                 bulk_commit();
             }
         }
@@ -792,7 +838,13 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    constexpr bool coop = (N >= 16) || (N == 8 && V == 1);
+    constexpr bool coop = ((N >= 16) || (N == 8 && V == 1)) && V != TC_V;
+    TcLane tcl;
+    uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NCONS / 32) * TC_ZS);
+    if constexpr (V == TC_V) {
+        tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r);
+        named_sync(1, NCONS);  // the table is written before any warp reads it
+    }
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
         uint8_t *buf;
@@ -817,22 +869,25 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                     if (y < hv && x + 8 <= wv) {
                         v = *reinterpret_cast<const uint2 *>(src + int64_t(y) * g.ld + x);
                     } else if (y < hv && x < wv) {  // ragged edge: only bytes inside the image
-                        uint32_t b[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-                        for (int e = 0; e < wv - x; e++) b[e] = src[int64_t(y) * g.ld + x + e];
-                        v.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-                        v.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+                        for (int e = 0; e < wv - x; e++) {
+                            const uint32_t b = src[int64_t(y) * g.ld + x + e];
+                            if (e < 4) v.x |= b << (8 * e);
+                            else v.y |= b << (8 * (e - 4));
+                        }
                     }
-                    *reinterpret_cast<uint2 *>(buf + y * TW + x) = v;
+                    *reinterpret_cast<uint2 *>(buf + tile_off<V>(y, x)) = v;
                 }
             } else {
                 for (int q = tid; q < TILE_BYTES; q += NCONS) {
                     const int y = q / TW, x = q - y * TW;
-                    buf[q] = (y < hv && x < wv) ? src[int64_t(y) * g.ld + x] : uint8_t(0);
+                    buf[tile_off<V>(y, x)] = (y < hv && x < wv) ? src[int64_t(y) * g.ld + x] : uint8_t(0);
                 }
             }
             named_sync(1, NCONS);
         }
-        float v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
+        float v;
+        if constexpr (V == TC_V) v = tile_tc(tcl, tctab, g, buf, tile, tid, Zs);
+        else v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
         if (g.use_tma) {
             // warp partial -> red[s][warp]; the producer sums the eight in order
 #pragma unroll
@@ -853,15 +908,16 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                     const int y = q / (TW / 8), x = (q - y * (TW / 8)) * 8;
                     if (y < hv && x + 8 <= wv) {
                         *reinterpret_cast<uint2 *>(dst + int64_t(y) * g.ld_recon + x) =
-                            *reinterpret_cast<const uint2 *>(buf + y * TW + x);
+                            *reinterpret_cast<const uint2 *>(buf + tile_off<V>(y, x));
                     } else if (y < hv && x < wv) {
-                        for (int e = 0; e < wv - x; e++) dst[int64_t(y) * g.ld_recon + x + e] = buf[y * TW + x + e];
+                        for (int e = 0; e < wv - x; e++)
+                            dst[int64_t(y) * g.ld_recon + x + e] = buf[tile_off<V>(y, x + e)];
                     }
                 }
             } else {
                 for (int q = tid; q < TILE_BYTES; q += NCONS) {
                     const int y = q / TW, x = q - y * TW;
-                    if (y < hv && x < wv) dst[int64_t(y) * g.ld_recon + x] = buf[q];
+                    if (y < hv && x < wv) dst[int64_t(y) * g.ld_recon + x] = buf[tile_off<V>(y, x)];
                 }
             }
         }
@@ -945,23 +1001,30 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     };
     bool tma = !a.force_plain && is16(a.img, a.ld, g.img_stride) &&
                (!a.recon || is16(a.recon, a.ld_recon, g.recon_stride));
+    const int V = fused_variant(N, g.D);
+    const bool swz = V == TC_V;
+    const int box_w = swz ? TW / 2 : TW;
     CUtensorMap tin{}, tout{};
     if (tma) {
-        tma = make_map_u8(&tin, a.img, a.W, a.H, a.nimg, a.ld, g.img_stride, TW, TH);
-        if (tma && a.recon) tma = make_map_u8(&tout, a.recon, a.W, a.H, a.nimg, a.ld_recon, g.recon_stride, TW, TH);
+        tma = make_map_u8(&tin, a.img, a.W, a.H, a.nimg, a.ld, g.img_stride, box_w, TH, swz);
+        if (tma && a.recon)
+            tma = make_map_u8(&tout, a.recon, a.W, a.H, a.nimg, a.ld_recon, g.recon_stride, box_w, TH, swz);
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    g.stages = (N >= 16) ? 3 : STAGES;
+    g.stages = swz ? 6 : ((N >= 16) ? 3 : 4);
     const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D);
-    const int V = fused_variant(N, g.D);
     const void *fn = nullptr;
     if constexpr (N == 4) fn = reinterpret_cast<const void *>(fused_kernel<4, 0>);
     else if constexpr (N == 8) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<8, 0>)
                                            : reinterpret_cast<const void *>(fused_kernel<8, 1>);
-    else fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
-                     : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
-                               : reinterpret_cast<const void *>(fused_kernel<N, 3>));
+    else {
+        fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
+                    : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
+                              : reinterpret_cast<const void *>(fused_kernel<N, 3>));
+        if constexpr (N == 32)
+            if (V == TC_V) fn = reinterpret_cast<const void *>(fused_kernel<32, TC_V>);
+    }
     const int dev = ensure_smem_attr(fn);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NCONS + 32, L.total);

@@ -79,7 +79,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D uint8 tensor map (x = column, y = row, z = image) with a box_w x box_h x 1 box.
 bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64_t ld, int64_t stride, int box_w,
-                 int box_h) {
+                 int box_h, bool swizzle128) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {cuuint64_t(W), cuuint64_t(H), cuuint64_t(nimg)};
@@ -87,7 +87,8 @@ bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64
     cuuint32_t box[3] = {cuuint32_t(box_w), cuuint32_t(box_h), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
