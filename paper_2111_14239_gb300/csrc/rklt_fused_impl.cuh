@@ -841,8 +841,10 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     constexpr bool coop = ((N >= 16) || (N == 8 && V == 1)) && V != TC_V;
     TcLane tcl;
     uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NCONS / 32) * TC_ZS);
+    const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
+    const uint32_t tczs = smem_u32(Zs + (tid >> 5) * TC_ZS);
     if constexpr (V == TC_V) {
-        tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r);
+        tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
         named_sync(1, NCONS);  // the table is written before any warp reads it
     }
     int64_t it = 0;
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             named_sync(1, NCONS);
         }
         float v;
-        if constexpr (V == TC_V) v = tile_tc(tcl, tctab, g, buf, tile, tid, Zs);
+        if constexpr (V == TC_V) v = tile_tc(tcl, tctabl, g, buf, tile, tid, tczs);
         else v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
         if (g.use_tma) {
             // warp partial -> red[s][warp]; the producer sums the eight in order

@@ -87,20 +87,56 @@ __device__ __forceinline__ void split_pair(float v0, float v1, uint32_t &hi, uin
     lo = as_u32(__floats2half2_rn(sub_f_h(v0, __low2half(h)), sub_f_h(v1, __high2half(h))));
 }
 
-// Per-lane constant operands of the forward passes, kept in registers.
+// Shared-memory accesses through 32-bit shared-window addresses.
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+template <int OFF>
+__device__ __forceinline__ uint32_t lds32o(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts32o(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0+%1], %2;" ::"r"(a), "n"(OFF), "r"(v));
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+
+// Per-lane constants kept in registers: F1's accumulator start and the lane's
+// shared-memory offsets inside a tile.
 struct TcLane {
-    uint32_t a1[2][4];   // F1 A fragments per k-step: T[j][x], rows j = 2g (even), 2g + 1 (odd)
-    float init1[2];      // F1 accumulator start for those rows: -1024 sum_x T[j][x]
-    uint32_t b2[2][2];   // F2 B per n-tile (even i, odd i): 2^-12 T[i][y], y < 16
+    float init1[2];      // F1 accumulator start for rows j = 2g, 2g + 1: -1024 sum_x T[j][x]
+    // byte offsets in the tile of the lane's words for the warp's block column:
+    // [class][word]; class 0 = row g (row 8 + g is +1024), class 1 = row 31 - g
+    // (row 23 - g is -1024); word 0 = x 4t..4t+3, 1 = x 16+4t.., 2 = x 28-4t..31-4t
+    uint32_t off[2][3];
 };
 
-// The other per-lane constants live in a shared-memory table of 8 x 32 uint4,
+// The other per-lane constants live in a shared-memory table of TC_TAB x 32 uint4,
 // entry [k][lane] (16-byte loads by consecutive lanes hit distinct banks):
 //   k = 0, 1  I1 B of y' n-tile k: hi, lo of 2^6 T^{-1}[y'][i] (even i), then (odd i)
 //   k = 2, 3  I2 B of x' n-tile k - 2: the same for T^{-1}[x'][j]
-//   k = 4, 5  zig-zag positions of accumulator elements q = 4 (k - 4) .. + 3, -1 if dropped
+//   k = 4, 5  staging slots of accumulator elements q = 4 (k - 4) .. + 3: the zig-zag
+//             position when retained, else the spare slot TC_ZS - 1
 //   k = 6, 7  2^12 s_i s_j of those elements
-constexpr int TC_TAB_BYTES = 8 * 32 * 16;
+//   k = 8, 9  1.0 when retained, else 0.0
+//   k = 10, 11  F1 A fragments of k-step k - 10: T[j][x], rows j = 2g (even), 2g + 1 (odd)
+//   k = 12    F2 B: 2^-12 T[i][y] (y < 16) for i = 2g (even n-tile), then i = 2g + 1
+constexpr int TC_TAB = 13;
+constexpr int TC_TAB_BYTES = TC_TAB * 32 * 16;
 
 __device__ __forceinline__ float tc_T(const PlanK<32> &P, int i, int x) {
     return x < 16 ? P.T[i][x] : ((i & 1) ? -P.T[i][31 - x] : P.T[i][31 - x]);
@@ -108,18 +144,11 @@ __device__ __forceinline__ float tc_T(const PlanK<32> &P, int i, int x) {
 
 // Builds the lane's registers and (when `write_tab`) its column of the table.
 // Element q = 4 * nt + e of a lane's F2 accumulator holds C[i][j] with
-// j = 2g + (e >> 1) and i = 4t + 2 (e & 1) + nt.
-__device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool write_tab, int lane, int r) {
+// j = 2g + (e >> 1) and i = 4t + 2 (e & 1) + nt.  bx is the warp's block column.
+__device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool write_tab, int lane, int r,
+                                int bx) {
     const int g = lane >> 2, t = lane & 3;
     const int j0 = 2 * g, j1 = 2 * g + 1;
-#pragma unroll
-    for (int ks = 0; ks < 2; ks++) {
-        const int x0 = 16 * ks + 4 * t;
-        c.a1[ks][0] = pack_h2(tc_T(P, j0, x0), tc_T(P, j0, x0 + 1));
-        c.a1[ks][1] = pack_h2(tc_T(P, j1, x0), tc_T(P, j1, x0 + 1));
-        c.a1[ks][2] = pack_h2(tc_T(P, j0, x0 + 2), tc_T(P, j0, x0 + 3));
-        c.a1[ks][3] = pack_h2(tc_T(P, j1, x0 + 2), tc_T(P, j1, x0 + 3));
-    }
     float s0 = 0.0f, s1 = 0.0f;
     for (int x = 0; x < 32; x++) {
         s0 += tc_T(P, j0, x);
@@ -128,13 +157,28 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
     c.init1[0] = -1024.0f * s0;
     c.init1[1] = -1024.0f * s1;
     const float q12 = 1.0f / 4096.0f, s6 = 64.0f;
+    const int cb = (bx & 3) * 2;
 #pragma unroll
-    for (int nt = 0; nt < 2; nt++) {
-        const int i = 2 * g + nt;
-        c.b2[nt][0] = pack_h2(q12 * P.T[i][2 * t], q12 * P.T[i][2 * t + 1]);
-        c.b2[nt][1] = pack_h2(q12 * P.T[i][2 * t + 8], q12 * P.T[i][2 * t + 9]);
+    for (int cls = 0; cls < 2; cls++) {
+        const int y = cls ? 31 - g : g, sw = y & 7;
+        const uint32_t rb = uint32_t((bx >> 2) * TC_HALF + y * 128);
+        c.off[cls][0] = rb + uint32_t(((cb ^ sw) << 4) + 4 * t);
+        c.off[cls][1] = rb + uint32_t((((cb + 1) ^ sw) << 4) + 4 * t);
+        c.off[cls][2] = rb + uint32_t((((cb + 1) ^ sw) << 4) + 12 - 4 * t);
     }
     if (!write_tab) return;
+#pragma unroll
+    for (int ks = 0; ks < 2; ks++) {
+        const int x0 = 16 * ks + 4 * t;
+        tab[(10 + ks) * 32 + lane] = make_uint4(pack_h2(tc_T(P, j0, x0), tc_T(P, j0, x0 + 1)),
+                                                pack_h2(tc_T(P, j1, x0), tc_T(P, j1, x0 + 1)),
+                                                pack_h2(tc_T(P, j0, x0 + 2), tc_T(P, j0, x0 + 3)),
+                                                pack_h2(tc_T(P, j1, x0 + 2), tc_T(P, j1, x0 + 3)));
+    }
+    tab[12 * 32 + lane] = make_uint4(pack_h2(q12 * P.T[j0][2 * t], q12 * P.T[j0][2 * t + 1]),
+                                     pack_h2(q12 * P.T[j0][2 * t + 8], q12 * P.T[j0][2 * t + 9]),
+                                     pack_h2(q12 * P.T[j1][2 * t], q12 * P.T[j1][2 * t + 1]),
+                                     pack_h2(q12 * P.T[j1][2 * t + 8], q12 * P.T[j1][2 * t + 9]));
 #pragma unroll
     for (int nt = 0; nt < 2; nt++) {
         const int yp = 8 * nt + g;                              // I1 n-tile column y'
@@ -147,52 +191,58 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
         tab[nt * 32 + lane] = v3;
         tab[(2 + nt) * 32 + lane] = v4;
     }
-    int zp[8];
-    float bs[8];
+    uint32_t zp[8], bs[8], kp[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const int nt = q >> 2, e = q & 3;
         const int j = 2 * g + (e >> 1), i = 4 * t + 2 * (e & 1) + nt;
         const int z = zz_index(32, i, j);
-        zp[q] = z < r ? z : -1;
-        bs[q] = 4096.0f * P.sij[i][j];
+        zp[q] = uint32_t(z < r ? z : TC_ZS - 1);
+        bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
+        kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
     }
-    tab[4 * 32 + lane] = make_uint4(zp[0], zp[1], zp[2], zp[3]);
-    tab[5 * 32 + lane] = make_uint4(zp[4], zp[5], zp[6], zp[7]);
-    tab[6 * 32 + lane] = make_uint4(__float_as_uint(bs[0]), __float_as_uint(bs[1]), __float_as_uint(bs[2]),
-                                    __float_as_uint(bs[3]));
-    tab[7 * 32 + lane] = make_uint4(__float_as_uint(bs[4]), __float_as_uint(bs[5]), __float_as_uint(bs[6]),
-                                    __float_as_uint(bs[7]));
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        tab[(4 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
+        tab[(6 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
+        tab[(8 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
+    }
 }
 
-// One 32 x 32 block (block row `by`, block column `bx` of the tile) by one warp.
-// Returns the lane's share of the block's SSE; writes the 8-bit reconstruction in
-// place when `recon`, and the r normalised coefficients to zg (if not null) through
-// the warp's staging buffer zs.
-__device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, uint8_t *tile, int by, int bx,
-                                            int lane, int r, float *zg, float *zs, bool recon, bool vec4) {
-    const int g = lane >> 2, t = lane & 3;
-    uint8_t *base = tile + (bx >> 2) * TC_HALF + by * 32 * 128;
-    const int cb = (bx & 3) * 2;  // first 16-byte chunk of the block in its half-tile row
-    // The lane's rows: F1 n-tile q and output row q are y = g, 8 + g, 31 - g, 23 - g
-    // (y mod 8 = g, g, 7 - g, 7 - g).
-    const auto row_ptr = [&](int q, int chunk, int byte) -> uint8_t * {
-        const int y = (q == 0) ? g : (q == 1) ? 8 + g : (q == 2) ? 31 - g : 23 - g;
-        const int s = q < 2 ? g : 7 - g;
-        return base + y * 128 + (((cb + chunk) ^ s) << 4) + byte;
+// One 32 x 32 block by one warp: `blk` is the shared-window address of the tile
+// plus 4096 * (block row); tabl is the table address plus 16 * lane; zs the warp's
+// staging buffer (shared-window address).  Returns the lane's share of the block's
+// SSE; writes the 8-bit reconstruction in place when `recon`, and the r normalised
+// coefficients to zg (if not null).
+__device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, int r,
+                                            float *zg, uint32_t zs, bool recon, bool vec4) {
+    // the lane's rows: q = 0: g, 1: 8 + g, 2: 31 - g, 3: 23 - g
+    // rows q = 0, 1 are [off[0][.]] and [off[0][.] + 1024], rows 2, 3 [off[1][.]] and
+    // [off[1][.] - 1024]
+    const auto ld_word = [&](int q, int word) -> uint32_t {
+        const uint32_t a = blk + c.off[q >> 1][word];
+        return q == 0 ? lds32o<0>(a) : q == 1 ? lds32o<1024>(a) : q == 2 ? lds32o<0>(a) : lds32o<-1024>(a);
+    };
+    const auto st_word = [&](int q, int word, uint32_t v) {
+        const uint32_t a = blk + c.off[q >> 1][word];
+        if (q == 0) sts32o<0>(a, v);
+        else if (q == 1) sts32o<1024>(a, v);
+        else if (q == 2) sts32o<0>(a, v);
+        else sts32o<-1024>(a, v);
     };
 
     // ---- F1: Z^T = T A^T (16 frequencies j x 32 rows y), pixels biased by 1024
     float d1[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; nt++) {
+    {
+        const uint4 a0 = lds128(tabl + 10 * 512), a1 = lds128(tabl + 11 * 512);
         const float ci[4] = {c.init1[0], c.init1[0], c.init1[1], c.init1[1]};
-        const uint32_t w0 = *reinterpret_cast<const uint32_t *>(row_ptr(nt, 0, 4 * t));
-        const uint32_t w1 = *reinterpret_cast<const uint32_t *>(row_ptr(nt, 1, 4 * t));
-        mma16(d1[nt], ci, c.a1[0][0], c.a1[0][1], c.a1[0][2], c.a1[0][3], bytes_to_biased_h2(w0, 0, 1),
-              bytes_to_biased_h2(w0, 2, 3));
-        mma16(d1[nt], d1[nt], c.a1[1][0], c.a1[1][1], c.a1[1][2], c.a1[1][3], bytes_to_biased_h2(w1, 0, 1),
-              bytes_to_biased_h2(w1, 2, 3));
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const uint32_t w0 = ld_word(nt, 0), w1 = ld_word(nt, 1);
+            mma16(d1[nt], ci, a0.x, a0.y, a0.z, a0.w, bytes_to_biased_h2(w0, 0, 1), bytes_to_biased_h2(w0, 2, 3));
+            mma16(d1[nt], d1[nt], a1.x, a1.y, a1.z, a1.w, bytes_to_biased_h2(w1, 0, 1),
+                  bytes_to_biased_h2(w1, 2, 3));
+        }
     }
     // ---- y-parity: S = Z[y] + Z[31-y], Dd = Z[y] - Z[31-y] (y < 16), as binary16 digits
     const float2 neg1 = make_float2(-1.0f, -1.0f);
@@ -211,40 +261,38 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
     // ---- F2: C^T * 2^-12 (rows j, columns i: n-tile 0 even i, n-tile 1 odd i)
     const float z4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     float d2[2][4];
-    mma16(d2[0], z4, sh[0][0], sh[0][1], sh[1][0], sh[1][1], c.b2[0][0], c.b2[0][1]);
-    mma16(d2[0], d2[0], sl[0][0], sl[0][1], sl[1][0], sl[1][1], c.b2[0][0], c.b2[0][1]);
-    mma16(d2[1], z4, dh[0][0], dh[0][1], dh[1][0], dh[1][1], c.b2[1][0], c.b2[1][1]);
-    mma16(d2[1], d2[1], dl[0][0], dl[0][1], dl[1][0], dl[1][1], c.b2[1][0], c.b2[1][1]);
-    // ---- M: coefficients (staged in zig-zag order), zonal mask, C' as binary16 digits
-    uint32_t ch[2][2], cl[2][2];
     {
-        const uint4 zp0 = tab[4 * 32 + lane], zp1 = tab[5 * 32 + lane];
-        const int zp[8] = {int(zp0.x), int(zp0.y), int(zp0.z), int(zp0.w),
-                           int(zp1.x), int(zp1.y), int(zp1.z), int(zp1.w)};
+        const uint4 b2 = lds128(tabl + 12 * 512);
+        mma16(d2[0], z4, sh[0][0], sh[0][1], sh[1][0], sh[1][1], b2.x, b2.y);
+        mma16(d2[0], d2[0], sl[0][0], sl[0][1], sl[1][0], sl[1][1], b2.x, b2.y);
+        mma16(d2[1], z4, dh[0][0], dh[0][1], dh[1][0], dh[1][1], b2.z, b2.w);
+        mma16(d2[1], d2[1], dl[0][0], dl[0][1], dl[1][0], dl[1][1], b2.z, b2.w);
+    }
+    // ---- M: coefficients staged in zig-zag order (dropped ones land in the spare
+    //      slot), zonal mask, C' as binary16 digits
+    uint32_t ch[2][2], cl[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++) {
         if (zg) {
-            const uint4 b0 = tab[6 * 32 + lane], b1 = tab[7 * 32 + lane];
-            const float bs[8] = {__uint_as_float(b0.x), __uint_as_float(b0.y), __uint_as_float(b0.z),
-                                 __uint_as_float(b0.w), __uint_as_float(b1.x), __uint_as_float(b1.y),
-                                 __uint_as_float(b1.z), __uint_as_float(b1.w)};
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (zp[q] >= 0) zs[zp[q]] = bs[q] * d2[q >> 2][q & 3];
+            const uint4 zp = lds128(tabl + (4 + nt) * 512), bs = lds128(tabl + (6 + nt) * 512);
+            sts_f32(zs + 4 * zp.x, __uint_as_float(bs.x) * d2[nt][0]);
+            sts_f32(zs + 4 * zp.y, __uint_as_float(bs.y) * d2[nt][1]);
+            sts_f32(zs + 4 * zp.z, __uint_as_float(bs.z) * d2[nt][2]);
+            sts_f32(zs + 4 * zp.w, __uint_as_float(bs.w) * d2[nt][3]);
         }
-#pragma unroll
-        for (int nt = 0; nt < 2; nt++) {
-#pragma unroll
-            for (int p = 0; p < 2; p++) {
-                const float v0 = zp[4 * nt + 2 * p] >= 0 ? d2[nt][2 * p] : 0.0f;
-                const float v1 = zp[4 * nt + 2 * p + 1] >= 0 ? d2[nt][2 * p + 1] : 0.0f;
-                split_pair(v0, v1, ch[nt][p], cl[nt][p]);
-            }
-        }
+        const uint4 kp = lds128(tabl + (8 + nt) * 512);
+        const float2 v0 = __fmul2_rn(make_float2(d2[nt][0], d2[nt][1]),
+                                     make_float2(__uint_as_float(kp.x), __uint_as_float(kp.y)));
+        const float2 v1 = __fmul2_rn(make_float2(d2[nt][2], d2[nt][3]),
+                                     make_float2(__uint_as_float(kp.z), __uint_as_float(kp.w)));
+        split_pair(v0.x, v0.y, ch[nt][0], cl[nt][0]);
+        split_pair(v1.x, v1.y, ch[nt][1], cl[nt][1]);
     }
     // ---- I1: E (even i) and O (odd i) for y' < 16; Y^T * 2^-6 = E + O (y'), E - O (31 - y')
     uint32_t yh[4][2], yl[4][2];  // [group][row half]: groups y' = 0..7, 8..15, 31..24, 23..16
 #pragma unroll
     for (int nt = 0; nt < 2; nt++) {
-        const uint4 b3 = tab[nt * 32 + lane];
+        const uint4 b3 = lds128(tabl + nt * 512);
         float E[4], O[4];
         mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], b3.x, b3.x);
         mma8(E, ch[0][0], ch[0][1], b3.y);
@@ -274,7 +322,7 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
         float E2[2][4], O2[2][4];  // [n-tile][4]
 #pragma unroll
         for (int nt = 0; nt < 2; nt++) {
-            const uint4 b4 = tab[(2 + nt) * 32 + lane];
+            const uint4 b4 = lds128(tabl + (2 + nt) * 512);
             mma16(E2[nt], half4, ah0, ah1, al0, al1, b4.x, b4.x);
             mma8(E2[nt], ah0, ah1, b4.y);
             mma16(O2[nt], z4, oh0, oh1, ol0, ol1, b4.z, b4.z);
@@ -283,15 +331,13 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int q = 2 * mt + h;
-            uint32_t *pt = reinterpret_cast<uint32_t *>(row_ptr(q, 0, 4 * t));
-            uint32_t *pb = reinterpret_cast<uint32_t *>(row_ptr(q, 1, 12 - 4 * t));
             const float2 e0 = make_float2(E2[0][2 * h], E2[0][2 * h + 1]);
             const float2 o0 = make_float2(O2[0][2 * h], O2[0][2 * h + 1]);
             const float2 e1 = make_float2(E2[1][2 * h], E2[1][2 * h + 1]);
             const float2 o1 = make_float2(O2[1][2 * h], O2[1][2 * h + 1]);
             const float2 ta = __fadd2_rn(e0, o0), tb = __fadd2_rn(e1, o1);              // x' = 4t + {0,1}, {2,3}
             const float2 ba = __ffma2_rn(o0, neg1, e0), bb = __ffma2_rn(o1, neg1, e1);  // bytes {3,2}, {1,0}
-            const uint32_t wt = *pt, wb = *pb;
+            const uint32_t wt = ld_word(q, 0), wb = ld_word(q, 2);
             const __half2 p01 = __hsub2(as_h2(bytes_to_biased_h2(wt, 0, 1)), k10235);   // pixel + 1/2
             const __half2 p23 = __hsub2(as_h2(bytes_to_biased_h2(wt, 2, 3)), k10235);
             const __half2 q01 = __hsub2(as_h2(bytes_to_biased_h2(wb, 0, 1)), k10235);
@@ -305,10 +351,10 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
             sse2 = __ffma2_rn(eb0, eb0, sse2);
             sse2 = __ffma2_rn(eb1, eb1, sse2);
             if (recon) {
-                *pt = floor_sat_u8(ta.x) | (floor_sat_u8(ta.y) << 8) | (floor_sat_u8(tb.x) << 16) |
-                      (floor_sat_u8(tb.y) << 24);
-                *pb = floor_sat_u8(bb.y) | (floor_sat_u8(bb.x) << 8) | (floor_sat_u8(ba.y) << 16) |
-                      (floor_sat_u8(ba.x) << 24);
+                st_word(q, 0, __byte_perm(__byte_perm(floor_sat_u8(ta.x), floor_sat_u8(ta.y), 0x0040),
+                                          __byte_perm(floor_sat_u8(tb.x), floor_sat_u8(tb.y), 0x0040), 0x5410));
+                st_word(q, 2, __byte_perm(__byte_perm(floor_sat_u8(bb.y), floor_sat_u8(bb.x), 0x0040),
+                                          __byte_perm(floor_sat_u8(ba.y), floor_sat_u8(ba.x), 0x0040), 0x5410));
             }
         }
     }
@@ -316,10 +362,12 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
     if (zg) {
         __syncwarp();
         if (vec4) {
-            for (int k = 4 * lane; k < r; k += 128)
-                *reinterpret_cast<float4 *>(zg + k) = *reinterpret_cast<const float4 *>(zs + k);
+            for (int k = 4 * lane; k < r; k += 128) {
+                const uint4 v = lds128(zs + 4 * k);
+                *reinterpret_cast<uint4 *>(zg + k) = v;
+            }
         } else {
-            for (int k = lane; k < r; k += 32) zg[k] = zs[k];
+            for (int k = lane; k < r; k += 32) zg[k] = __uint_as_float(lds32(zs + 4 * k));
         }
         __syncwarp();
     }
@@ -327,13 +375,14 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, const uint4 *tab, u
 }
 
 // All blocks of one tile: warp w takes block column w of both block rows.
-__device__ __forceinline__ float tile_tc(const TcLane &c, const uint4 *tab, const FusedGeom &g, uint8_t *tile,
-                                         int64_t tile_id, int ct, float *Zs) {
+__device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
+                                         int64_t tile_id, int ct, uint32_t zs) {
     const TileCoord tc = tile_coord(g, tile_id);
     const int w = ct >> 5, lane = ct & 31;
     const int bw = g.W / 32;
     const int rows_in = min(TH / 32, (g.H - tc.ty * TH) / 32);
     const int nb_in = min(TW / 32, bw - tc.tx * (TW / 32));
+    const uint32_t t32 = smem_u32(tile);
     float sse = 0.0f;
     if (w < nb_in) {
         for (int by = 0; by < rows_in; by++) {
@@ -341,7 +390,7 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, const uint4 *tab, cons
                                              int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + w) *
                                                 g.r
                                 : nullptr;
-            sse += tc_block32(c, tab, tile, by, w, lane, g.r, zg, Zs + w * TC_ZS, g.recon != nullptr,
+            sse += tc_block32(c, tabl, t32 + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
                               g.coef_vec4 != 0);
         }
     }
