@@ -638,12 +638,13 @@ namespace rklt {
 
 // Kernel variant V (picked on the host from the diagonal bound D):
 //   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), 1 cooperative;
-//   N = 32 with D <= 16: TC_V (tensor cores, one warp per block);
+//   N = 32 with D <= 16, N = 16 with D <= 8: TC_V (tensor cores);
 //   N >= 16 otherwise: 1, 2, 3 = cooperative path sized for Dr <= N/4, N/2, N.
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
     if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
     if (N == 32 && D <= TC_DMAX) return TC_V;
+    if (N == 16 && D <= TC_DMAX16) return TC_V;
     const int Dr = D < N ? D : N;
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
@@ -844,7 +845,8 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
     const uint32_t tczs = smem_u32(Zs + (tid >> 5) * TC_ZS);
     if constexpr (V == TC_V) {
-        tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
+        if constexpr (N == 32) tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
+        else tc16_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
         named_sync(1, NCONS);  // the table is written before any warp reads it
     }
     int64_t it = 0;
@@ -888,7 +890,10 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
             named_sync(1, NCONS);
         }
         float v;
-        if constexpr (V == TC_V) v = tile_tc(tcl, tctabl, g, buf, tile, tid, tczs);
+        if constexpr (V == TC_V) {
+            if constexpr (N == 32) v = tile_tc(tcl, tctabl, g, buf, tile, tid, tczs);
+            else v = tile_tc16(tcl, tctabl, g, buf, tile, tid, tczs);
+        }
         else v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
         if (g.use_tma) {
             // warp partial -> red[s][warp]; the producer sums the eight in order
@@ -1024,8 +1029,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
                     : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
                               : reinterpret_cast<const void *>(fused_kernel<N, 3>));
-        if constexpr (N == 32)
-            if (V == TC_V) fn = reinterpret_cast<const void *>(fused_kernel<32, TC_V>);
+        if (V == TC_V) fn = reinterpret_cast<const void *>(fused_kernel<N, TC_V>);
     }
     const int dev = ensure_smem_attr(fn);
     int per_sm = 0;

@@ -1,6 +1,8 @@
-// rklt_tc.cuh -- 32 x 32 blocks on the tensor cores (warp-level fp16 mma.sync with
-// fp32 accumulation) for retained supports inside i + j < 16 (r <= 136).  Included by
-// rklt_fused_impl.cuh after the tile constants; used by fused_kernel<32, TC_V>.
+// rklt_tc.cuh -- 32 x 32 and 16 x 16 blocks on the tensor cores (warp-level fp16
+// mma.sync with fp32 accumulation): N = 32 with retained supports inside i + j < 16
+// (r <= 136), N = 16 inside i + j < 8 (r <= 36).  Included by rklt_fused_impl.cuh
+// after the tile constants; used by fused_kernel<32, TC_V> and fused_kernel<16, TC_V>.
+// The N = 32 chain is described first; the N = 16 form follows at tc16_setup.
 //
 // One warp transforms one block.  Lane l has g = l / 4 and t = l % 4, the MMA
 // fragment coordinates.  The chain of contractions (Sec. 4.1: C = T A T^T, zonal
@@ -34,9 +36,10 @@
 namespace rklt {
 
 constexpr int TC_V = 4;                    // kernel variant number of this path
-constexpr int TC_DMAX = 16;                // handles diagonal bounds D <= 16
+constexpr int TC_DMAX = 16;                // N = 32: handles diagonal bounds D <= 16
+constexpr int TC_DMAX16 = 8;               // N = 16: handles D <= 8
 constexpr int TC_HALF = (TW / 2) * TH;     // bytes of one 128-byte-wide half tile
-constexpr int TC_ZS = 140;                 // per-warp coefficient staging stride (floats)
+constexpr int TC_ZS = 148;                 // per-warp coefficient staging stride (floats)
 
 // Byte offset of pixel (y, x) of a 64 x 256 tile held as two 64 x 128 halves, each
 // in the 128-byte swizzled layout of a TMA copy: the 16-byte chunk index of row y is
@@ -392,6 +395,280 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
                                 : nullptr;
             sse += tc_block32(c, tabl, t32 + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
                               g.coef_vec4 != 0);
+        }
+    }
+    return sse;
+}
+
+// ---------------------------------------------------------------------------
+// N = 16: one warp takes a 32 x 32 region of four blocks (vb, hb) (block row, block
+// column) and runs the same chain with the block index folded into the MMA shapes:
+//   F1  rows (hb, j), j < 8; k-step hb' = x block; the A operand is block diagonal
+//       (T[j][x] where hb = hb', else 0), so each row sums its own block's columns
+//   F2  per class (even i from S = Z[y] + Z[15-y], odd i from Z[y] - Z[15-y]) and per
+//       k-step vb: K = (digit, y < 8), columns (vb', i) with B zero unless vb' = vb
+//   I1  K = D2 columns (vb, i) of one class with [hi | lo] digits, columns (vb3, y'),
+//       y' < 8, B zero unless vb = vb3; E (even i) + O (odd i) and E - O give rows
+//       y' and 15 - y' of block row vb3
+//   I2  per block column hb: the transposed 8 x 8 digit blocks (rows y, columns j)
+//       times 2^6 T^{-1}[x][j] for all 16 x, 4 adjacent x per lane
+// Row order of the lane: q = 0: y = g, 1: 16 + g, 2: 15 - g, 3: 31 - g (region rows).
+//
+// Table entries [k][lane] (uint4):
+//   k = 0   F1 A: (T[g][4t], T[g][4t+1]), (T[g][4t+2], T[g][4t+3]); F2 B for class 0
+//           and 1: 2^-12 (T[i][2t], T[i][2t+1]) with i = 2 (g & 3) + class (lanes with
+//           g >> 2 = vb carry the k-step vb's nonzero entries)
+//   k = 1   I1 B, class 0 (even i): hi, lo for column block vb3 = 0, then vb3 = 1
+//   k = 2   I1 B, class 1 (odd i)
+//   k = 3   I2 B: hi, lo of 2^6 T^{-1}[x][2t, 2t+1] for n-tile 0, then n-tile 1
+//   k = 4..5  staging slots (2 vb + hb) r + z of accumulator elements q = 4 class + e
+//   k = 6..7  2^12 s_i s_j;  k = 8..9  1.0 when retained, else 0.0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tc16_T(const PlanK<16> &P, int i, int x) {
+    return x < 8 ? P.T[i][x] : ((i & 1) ? -P.T[i][15 - x] : P.T[i][15 - x]);
+}
+__device__ __forceinline__ float tc16_Ti(const PlanK<16> &P, int l, int j) {  // T^{-1}[l][j], any l
+    return l < 8 ? P.Ti[l][j] : ((j & 1) ? -P.Ti[15 - l][j] : P.Ti[15 - l][j]);
+}
+
+__device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, bool write_tab, int lane, int r,
+                                  int bx) {
+    const int g = lane >> 2, t = lane & 3;
+    float s0 = 0.0f;
+    for (int x = 0; x < 16; x++) s0 += tc16_T(P, g, x);
+    c.init1[0] = c.init1[1] = -1024.0f * s0;
+    const int cb = (bx & 3) * 2;
+#pragma unroll
+    for (int cls = 0; cls < 2; cls++) {
+        const int y = cls ? 15 - g : g, sw = y & 7;
+        const uint32_t rb = uint32_t((bx >> 2) * TC_HALF + y * 128);
+        c.off[cls][0] = rb + uint32_t(((cb ^ sw) << 4) + 4 * t);
+        c.off[cls][1] = rb + uint32_t((((cb + 1) ^ sw) << 4) + 4 * t);
+        c.off[cls][2] = 0;
+    }
+    if (!write_tab) return;
+    const float q12 = 1.0f / 4096.0f, s6 = 64.0f;
+    const int i0 = 2 * (g & 3), i1 = 2 * (g & 3) + 1;
+    tab[0 * 32 + lane] = make_uint4(pack_h2(tc16_T(P, g, 4 * t), tc16_T(P, g, 4 * t + 1)),
+                                    pack_h2(tc16_T(P, g, 4 * t + 2), tc16_T(P, g, 4 * t + 3)),
+                                    pack_h2(q12 * P.T[i0][2 * t], q12 * P.T[i0][2 * t + 1]),
+                                    pack_h2(q12 * P.T[i1][2 * t], q12 * P.T[i1][2 * t + 1]));
+#pragma unroll
+    for (int cls = 0; cls < 2; cls++) {
+        // K index k = 2t, 2t+1 <-> D2 column (vb = t >> 1, i = 4 (t & 1) + {0, 2} + cls)
+        const int ia = 4 * (t & 1) + cls, ib = ia + 2;
+        uint32_t h, l;
+        split_pair(s6 * P.Ti[g][ia], s6 * P.Ti[g][ib], h, l);
+        const bool v0 = (t >> 1) == 0;
+        tab[(1 + cls) * 32 + lane] = make_uint4(v0 ? h : 0u, v0 ? l : 0u, v0 ? 0u : h, v0 ? 0u : l);
+    }
+    {
+        uint4 v;
+        const int xa = 4 * (g >> 1) + (g & 1), xb = xa + 2;  // n-tile 0 and 1 columns x
+        split_pair(s6 * tc16_Ti(P, xa, 2 * t), s6 * tc16_Ti(P, xa, 2 * t + 1), v.x, v.y);
+        split_pair(s6 * tc16_Ti(P, xb, 2 * t), s6 * tc16_Ti(P, xb, 2 * t + 1), v.z, v.w);
+        tab[3 * 32 + lane] = v;
+    }
+    uint32_t zp[8], bs[8], kp[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const int cls = q >> 2, e = q & 3;
+        const int vb = t >> 1, hb = e >> 1;
+        const int i = 2 * ((2 * t + (e & 1)) & 3) + cls, j = g;
+        const int z = zz_index(16, i, j);
+        zp[q] = uint32_t(z < r ? (2 * vb + hb) * r + z : TC_ZS - 1);
+        bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
+        kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        tab[(4 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
+        tab[(6 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
+        tab[(8 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
+    }
+}
+
+// One 32 x 32 region (four 16 x 16 blocks) by one warp.  `in` has bit 2 vb + hb set
+// for the blocks inside the image (all four in the interior); only those add to the
+// SSE.  The staging buffer receives each block's r coefficients at (2 vb + hb) r.
+template <bool ALL_IN>
+__device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, uint32_t zs,
+                                             bool coef, bool recon, int in) {
+    const int t = lane & 3;
+    // word w (x block) of row q: q = 0 [off[0][w]], 1 [+2048], 2 [off[1][w]], 3 [+2048]
+    const auto ld_word = [&](int q, int w) -> uint32_t {
+        const uint32_t a = blk + c.off[q >> 1 ? 1 : 0][w];
+        return (q & 1) ? lds32o<2048>(a) : lds32o<0>(a);
+    };
+    const auto st_word = [&](int q, int w, uint32_t v) {
+        const uint32_t a = blk + c.off[q >> 1 ? 1 : 0][w];
+        if (q & 1) sts32o<2048>(a, v);
+        else sts32o<0>(a, v);
+    };
+    // ---- F1 (n-tiles 0..3 = rows y = g, 15 - g, 16 + g, 31 - g = lane rows q 0, 2, 1, 3)
+    const uint4 k0 = lds128(tabl);
+    float d1[4][4];
+    {
+        const float ci[4] = {c.init1[0], c.init1[0], c.init1[0], c.init1[0]};
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const int q = (nt == 0) ? 0 : (nt == 1) ? 2 : (nt == 2) ? 1 : 3;
+            const uint32_t w0 = ld_word(q, 0), w1 = ld_word(q, 1);
+            mma16(d1[nt], ci, k0.x, 0u, k0.y, 0u, bytes_to_biased_h2(w0, 0, 1), bytes_to_biased_h2(w0, 2, 3));
+            mma16(d1[nt], d1[nt], 0u, k0.x, 0u, k0.y, bytes_to_biased_h2(w1, 0, 1), bytes_to_biased_h2(w1, 2, 3));
+        }
+    }
+    // ---- y-parity per block row vb: S = Z[y'] + Z[15-y'], Dd = Z[y'] - Z[15-y'], digits
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    uint32_t sh[2][2], sl[2][2], dh[2][2], dl[2][2];  // [vb][row half = hb]
+#pragma unroll
+    for (int vb = 0; vb < 2; vb++) {
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            const float2 u = make_float2(d1[2 * vb][2 * p], d1[2 * vb][2 * p + 1]);
+            const float2 v = make_float2(d1[2 * vb + 1][2 * p], d1[2 * vb + 1][2 * p + 1]);
+            const float2 s = __fadd2_rn(u, v), d = __ffma2_rn(v, neg1, u);
+            split_pair(s.x, s.y, sh[vb][p], sl[vb][p]);
+            split_pair(d.x, d.y, dh[vb][p], dl[vb][p]);
+        }
+    }
+    // ---- F2: class 0 (even i) from S, class 1 (odd i) from Dd; k-step vb
+    const float z4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float d2[2][4];
+    {
+        const int vbl = (lane >> 2) >> 2;  // the k-step whose B entries this lane holds
+        const uint32_t e0 = vbl == 0 ? k0.z : 0u, e1 = vbl == 1 ? k0.z : 0u;
+        const uint32_t o0 = vbl == 0 ? k0.w : 0u, o1 = vbl == 1 ? k0.w : 0u;
+        mma16(d2[0], z4, sh[0][0], sh[0][1], sl[0][0], sl[0][1], e0, e0);
+        mma16(d2[0], d2[0], sh[1][0], sh[1][1], sl[1][0], sl[1][1], e1, e1);
+        mma16(d2[1], z4, dh[0][0], dh[0][1], dl[0][0], dl[0][1], o0, o0);
+        mma16(d2[1], d2[1], dh[1][0], dh[1][1], dl[1][0], dl[1][1], o1, o1);
+    }
+    // ---- M: staged coefficients, zonal mask, C' digits
+    uint32_t ch[2][2], cl[2][2];
+#pragma unroll
+    for (int cls = 0; cls < 2; cls++) {
+        if (coef) {
+            const uint4 zp = lds128(tabl + (4 + cls) * 512), bs = lds128(tabl + (6 + cls) * 512);
+            sts_f32(zs + 4 * zp.x, __uint_as_float(bs.x) * d2[cls][0]);
+            sts_f32(zs + 4 * zp.y, __uint_as_float(bs.y) * d2[cls][1]);
+            sts_f32(zs + 4 * zp.z, __uint_as_float(bs.z) * d2[cls][2]);
+            sts_f32(zs + 4 * zp.w, __uint_as_float(bs.w) * d2[cls][3]);
+        }
+        const uint4 kp = lds128(tabl + (8 + cls) * 512);
+        const float2 v0 = __fmul2_rn(make_float2(d2[cls][0], d2[cls][1]),
+                                     make_float2(__uint_as_float(kp.x), __uint_as_float(kp.y)));
+        const float2 v1 = __fmul2_rn(make_float2(d2[cls][2], d2[cls][3]),
+                                     make_float2(__uint_as_float(kp.z), __uint_as_float(kp.w)));
+        split_pair(v0.x, v0.y, ch[cls][0], cl[cls][0]);
+        split_pair(v1.x, v1.y, ch[cls][1], cl[cls][1]);
+    }
+    // ---- I1: n-tile vb3; top (y' < 8) = E + O, bottom (15 - y') = E - O
+    uint32_t yh[4][2], yl[4][2];  // groups q: 0 = vb0 top, 1 = vb1 top, 2 = vb0 bottom, 3 = vb1 bottom
+    {
+        const uint4 be = lds128(tabl + 1 * 512), bo = lds128(tabl + 2 * 512);
+#pragma unroll
+        for (int vb3 = 0; vb3 < 2; vb3++) {
+            const uint32_t eh = vb3 ? be.z : be.x, el = vb3 ? be.w : be.y;
+            const uint32_t oh = vb3 ? bo.z : bo.x, ol = vb3 ? bo.w : bo.y;
+            float E[4], O[4];
+            mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], eh, eh);
+            mma8(E, ch[0][0], ch[0][1], el);
+            mma16(O, z4, ch[1][0], ch[1][1], cl[1][0], cl[1][1], oh, oh);
+            mma8(O, ch[1][0], ch[1][1], ol);
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const float2 e2 = make_float2(E[2 * p], E[2 * p + 1]), o2 = make_float2(O[2 * p], O[2 * p + 1]);
+                const float2 top = __fadd2_rn(e2, o2), bot = __ffma2_rn(o2, neg1, e2);
+                split_pair(top.x, top.y, yh[vb3][p], yl[vb3][p]);
+                split_pair(bot.x, bot.y, yh[2 + vb3][p], yl[2 + vb3][p]);
+            }
+        }
+    }
+    // ---- I2 per (m-tile, block column hb), then error and 8-bit output.  m-tile mt has
+    //      rows g (group 2 mt) and g + 8 (group 2 mt + 1): y = g, 16 + g (mt 0) and
+    //      15 - g, 31 - g (mt 1); lane word x = 16 hb + 4t .. 4t + 3
+    const uint4 b4 = lds128(tabl + 3 * 512);
+    const __half2 k10235 = __float2half2_rn(1023.5f);
+    const float half4[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+    float2 sse2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+#pragma unroll
+        for (int hb = 0; hb < 2; hb++) {
+            const uint32_t ah0 = movm_t(yh[2 * mt][hb]), ah1 = movm_t(yh[2 * mt + 1][hb]);
+            const uint32_t al0 = movm_t(yl[2 * mt][hb]), al1 = movm_t(yl[2 * mt + 1][hb]);
+            float R[2][4];
+            mma16(R[0], half4, ah0, ah1, al0, al1, b4.x, b4.x);
+            mma8(R[0], ah0, ah1, b4.y);
+            mma16(R[1], half4, ah0, ah1, al0, al1, b4.z, b4.z);
+            mma8(R[1], ah0, ah1, b4.w);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int q = 2 * mt + h;            // group; region row y as listed above
+                const int vb = (q == 1 || q == 3) ? 1 : 0;
+                const float2 va = make_float2(R[0][2 * h], R[0][2 * h + 1]);   // x = 4t, 4t + 1
+                const float2 vc = make_float2(R[1][2 * h], R[1][2 * h + 1]);   // x = 4t + 2, 4t + 3
+                const int lq = (q == 0) ? 0 : (q == 1) ? 1 : (q == 2) ? 2 : 3;
+                // lane rows: ld_word's q follows y = g, 16 + g, 15 - g, 31 - g
+                const uint32_t wt = ld_word(lq, hb);
+                const __half2 p01 = __hsub2(as_h2(bytes_to_biased_h2(wt, 0, 1)), k10235);
+                const __half2 p23 = __hsub2(as_h2(bytes_to_biased_h2(wt, 2, 3)), k10235);
+                float2 e0 = make_float2(sub_h_f(__low2half(p01), va.x), sub_h_f(__high2half(p01), va.y));
+                float2 e1 = make_float2(sub_h_f(__low2half(p23), vc.x), sub_h_f(__high2half(p23), vc.y));
+                if (!ALL_IN && !((in >> (2 * vb + hb)) & 1)) e0 = e1 = make_float2(0.0f, 0.0f);
+                sse2 = __ffma2_rn(e0, e0, sse2);
+                sse2 = __ffma2_rn(e1, e1, sse2);
+                if (recon)
+                    st_word(lq, hb, __byte_perm(__byte_perm(floor_sat_u8(va.x), floor_sat_u8(va.y), 0x0040),
+                                                __byte_perm(floor_sat_u8(vc.x), floor_sat_u8(vc.y), 0x0040), 0x5410));
+            }
+        }
+    }
+    (void)t;
+    return sse2.x + sse2.y;
+}
+
+// All regions of one tile (N = 16): warp w takes region column w of both region rows.
+__device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
+                                           int64_t tile_id, int ct, uint32_t zs) {
+    const TileCoord tc = tile_coord(g, tile_id);
+    const int w = ct >> 5, lane = ct & 31;
+    const int bw = g.W / 16;
+    const int rows_in = min(TH / 16, (g.H - tc.ty * TH) / 16);   // block rows of the tile inside
+    const int nb_in = min(TW / 16, bw - tc.tx * (TW / 16));       // block columns inside
+    const uint32_t t32 = smem_u32(tile);
+    const int r = g.r;
+    float sse = 0.0f;
+    if (2 * w >= nb_in) return sse;
+    for (int ry = 0; ry < 2; ry++) {
+        if (2 * ry >= rows_in) break;
+        int in = 0;
+#pragma unroll
+        for (int vb = 0; vb < 2; vb++)
+#pragma unroll
+            for (int hb = 0; hb < 2; hb++)
+                if (2 * ry + vb < rows_in && 2 * w + hb < nb_in) in |= 1 << (2 * vb + hb);
+        const uint32_t blk = t32 + ry * 32 * 128;
+        const bool coef = g.zcoef != nullptr;
+        if (in == 15) sse += tc16_region<true>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        else sse += tc16_region<false>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        if (coef) {
+            __syncwarp();
+#pragma unroll
+            for (int vb = 0; vb < 2; vb++) {
+                if (!((in >> (2 * vb)) & 1)) continue;
+                const int n = ((in >> (2 * vb + 1)) & 1) ? 2 * r : r;   // floats of this block row
+                float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
+                                        int64_t(tc.ty * (TH / 16) + 2 * ry + vb) * bw + tc.tx * (TW / 16) + 2 * w) * r;
+                const uint32_t src = zs + 4 * (2 * vb * r);
+                if (g.coef_vec4) {
+                    for (int k = 4 * lane; k < n; k += 128) *reinterpret_cast<uint4 *>(dst + k) = lds128(src + 4 * k);
+                } else {
+                    for (int k = lane; k < n; k += 32) dst[k] = __uint_as_float(lds32(src + 4 * k));
+                }
+            }
+            __syncwarp();
         }
     }
     return sse;
