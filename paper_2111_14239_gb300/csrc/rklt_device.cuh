@@ -99,13 +99,30 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete sleeps
+// in hardware until the phase completes or about hint_ns pass, instead of spinning
+// (a spinning warp takes issue slots from the working warps of its scheduler).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for phase `parity` of an mbarrier, giving up after timeout_ns of GPU
-// time; on give-up the device status latches RKLT_ERR_TIMEOUT (7).
+// time; on give-up the device status latches RKLT_ERR_TIMEOUT (7).  Each retry
+// sleeps up to 0.5 ms (or the remaining limit, if shorter) unless the phase completes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
+    const uint32_t hint = timeout_ns < 500000ull ? uint32_t(timeout_ns) : 500000u;
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, hint)) return true;
         if (global_timer_ns() - t0 > timeout_ns) {
             atomicExch(&g_dev_status, 7u);
             return false;

@@ -47,7 +47,9 @@ constexpr int TW = 256;          // tile width in bytes (pixels)
 constexpr int TH = 64;           // tile height in rows
 constexpr int TILE_BYTES = TW * TH;
 constexpr int STAGES = 8;        // deepest TMA ring (barrier and reduction slots)
-constexpr int NCONS = 256;       // consumer threads (8 warps); one producer warp follows
+constexpr int NCONS = 256;       // consumer threads (8 warps) of the FMA variants; one producer warp follows
+constexpr int NCONS_TC = 256;    // consumer threads (8 warps) of the tensor-core variant
+constexpr int NCONS_MAX = 256;
 constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchange buffer (floats)
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
 constexpr int REG_DMAX8 = 5;     // N = 8: register path up to this diagonal bound
@@ -273,11 +275,34 @@ __device__ __forceinline__ TileCoord tile_coord(const FusedGeom &g, int64_t tile
     return t;
 }
 
+// Coordinates of the tiles a CTA visits (ids blockIdx.x, + gridDim.x, ...), advanced
+// with two carries per step instead of a 64-bit division per tile.  The grid stride
+// in (img, ty, tx) form comes with the launch (g.step_*, step_tx < tiles_x,
+// step_ty < tiles_y).
+struct TileWalker {
+    TileCoord c;
+    __device__ __forceinline__ void init(const FusedGeom &g) { c = tile_coord(g, blockIdx.x); }
+    __device__ __forceinline__ void next(const FusedGeom &g) {
+        c.tx += g.step_tx;
+        int carry = 0;
+        if (c.tx >= g.tiles_x) {
+            c.tx -= g.tiles_x;
+            carry = 1;
+        }
+        c.ty += g.step_ty + carry;
+        carry = 0;
+        if (c.ty >= g.tiles_y) {
+            c.ty -= g.tiles_y;
+            carry = 1;
+        }
+        c.img += g.step_img + carry;
+    }
+};
+
 template <int N>
-__device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
+__device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
-    const TileCoord tc = tile_coord(g, tile_id);
     const int bw = g.W / N;
     float sse = 0.0f;
 #pragma unroll 1
@@ -301,11 +326,10 @@ __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g,
 // contiguously.  D and r are runtime values.
 // ---------------------------------------------------------------------------
 template <int N>
-__device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
+__device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                            int ct, float *Ys, float *Zs) {
     constexpr int H2 = N / 2;
     constexpr int BPR = TW / N;
-    const TileCoord tc = tile_coord(g, tile_id);
     const int bw = g.W / N;
     const int D = g.D, r = g.r;
     const int Dr = D < N ? D : N;
@@ -444,13 +468,12 @@ __host__ __device__ inline bool coop2_stage_coef(int N, int r) {
 }
 
 template <int N, int DRM>
-__device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
+__device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct, float *Ys, float *Zs) {
     constexpr int H2 = N / 2;
     constexpr int R = TH / N;
     constexpr int NB = TW / N;
     constexpr int LB = N + 4;  // padded block row in Ys
-    const TileCoord tc = tile_coord(g, tile_id);
     const int bw = g.W / N;
     const int D = g.D, r = g.r;
     const int Dr = D < N ? D : N;
@@ -649,46 +672,50 @@ __host__ __device__ inline int fused_variant(int N, int D) {
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
 
+// Consumer threads of kernel variant V.
+__host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : NCONS; }
+
 template <int N, int V>
-__device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, int64_t tile_id,
+__device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                               int ct, float *Ys, float *Zs) {
     if constexpr (N == 4) {
-        return tile_reg<4>(P, g, tile, tile_id, ct);
+        return tile_reg<4>(P, g, tile, tc, ct);
     } else if constexpr (N == 8) {
-        if constexpr (V == 0) return tile_reg<8>(P, g, tile, tile_id, ct);
-        else return tile_coop<8>(P, g, tile, tile_id, ct, Ys, Zs);
+        if constexpr (V == 0) return tile_reg<8>(P, g, tile, tc, ct);
+        else return tile_coop<8>(P, g, tile, tc, ct, Ys, Zs);
     } else {
-        if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tile_id, ct, Ys, Zs);
-        else if constexpr (V == 2) return tile_coop2<N, N / 2>(P, g, tile, tile_id, ct, Ys, Zs);
-        else return tile_coop2<N, N>(P, g, tile, tile_id, ct, Ys, Zs);
+        if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tc, ct, Ys, Zs);
+        else if constexpr (V == 2) return tile_coop2<N, N / 2>(P, g, tile, tc, ct, Ys, Zs);
+        else return tile_coop2<N, N>(P, g, tile, tc, ct, Ys, Zs);
     }
 }
 
-// Sum of the eight consumer warps' partials of one tile, in warp order.
+// Sum of the NC / 32 consumer warps' partials of one tile, in warp order.
+template <int NC>
 __device__ __forceinline__ float sum_warp_partials(const float *w) {
     float t = 0.0f;
 #pragma unroll
-    for (int i = 0; i < NCONS / 32; i++) t += w[i];
+    for (int i = 0; i < NC / 32; i++) t += w[i];
     return t;
 }
 
-// Fixed-order reduction over the consumer threads; thread 0 returns the sum.
+// Fixed-order reduction over the NC consumer threads; thread 0 returns the sum.
+template <int NC>
 __device__ __forceinline__ float reduce_consumers(float v, float *red, int ct) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if ((ct & 31) == 0) red[ct >> 5] = v;
-    named_sync(2, NCONS);
+    named_sync(2, NC);
     float t = 0.0f;
     if (ct == 0) {
 #pragma unroll
-        for (int w = 0; w < NCONS / 32; w++) t += red[w];
+        for (int w = 0; w < NC / 32; w++) t += red[w];
     }
-    named_sync(2, NCONS);
+    named_sync(2, NC);
     return t;
 }
 
-__device__ __forceinline__ void tile_origin(const FusedGeom &g, int64_t tile_id, int &x, int &y, int &z) {
-    const TileCoord t = tile_coord(g, tile_id);
+__device__ __forceinline__ void tile_origin(const TileCoord &t, int &x, int &y, int &z) {
     z = t.img;
     y = t.ty * TH;
     x = t.tx * TW;
@@ -737,10 +764,10 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
     SmemLayout L{};
     L.bar_off = stages * TILE_BYTES;
     L.red_off = L.bar_off + 2 * STAGES * 8;
-    L.ys_off = L.red_off + STAGES * (NCONS / 32) * 4;  // barrier and reduction slots for the deepest ring
+    L.ys_off = L.red_off + STAGES * (NCONS_MAX / 32) * 4;  // barrier and reduction slots, deepest ring
     int ys = 0, zs = 0;
     if (fused_variant(N, D) == TC_V) {
-        zs = (NCONS / 32) * TC_ZS * 4 + TC_TAB_BYTES;
+        zs = (NCONS_TC / 32) * TC_ZS * 4 + TC_TAB_BYTES;
     } else if (N >= 16) {
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
@@ -758,9 +785,10 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
 // The kernel: warps 0..7 consume; warp 8 produces in TMA mode (idle otherwise).
 // ---------------------------------------------------------------------------
 template <int N, int V>
-__global__ void __launch_bounds__(NCONS + 32, 2)
+__global__ void __launch_bounds__(ncons(V) + 32, 2)
     fused_kernel(const __grid_constant__ PlanK<N> P, const __grid_constant__ CUtensorMap tm_in,
                  const __grid_constant__ CUtensorMap tm_out, const FusedGeom g) {
+    constexpr int NC = ncons(V);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NST = g.stages;  // ring depth (<= STAGES)
@@ -772,20 +800,23 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     float *Zs = reinterpret_cast<float *>(smem + L.zs_off);
     const int tid = threadIdx.x;
 
-    if (g.use_tma && tid == NCONS) {
+    if (g.use_tma && tid == NC) {
         for (int s = 0; s < NST; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NCONS / 32);
+            mbar_init(&empty[s], NC / 32);
         }
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (tid >= NCONS) {
+    if (tid >= NC) {
         // ---------------- producer: one elected lane of warp 8 ----------------
-        if (!g.use_tma || tid != NCONS) return;
+        if (!g.use_tma || tid != NC) return;
         int64_t it = 0;
         bool ok = true;
+        TileWalker lw, sw;  // tiles being loaded; tiles being written back (NST behind)
+        lw.init(g);
+        sw = lw;
         for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
             const int s = int(it % NST);
             if (it >= NST) {
@@ -795,18 +826,20 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                     break;
                 }
                 const int64_t prev = tile - int64_t(NST) * gridDim.x;
-                g.partials[prev] = sum_warp_partials(red + s * (NCONS / 32));
+                g.partials[prev] = sum_warp_partials<NC>(red + s * (NC / 32));
                 if (g.recon) {
                     int x, y, z;
-                    tile_origin(g, prev, x, y, z);
+                    tile_origin(sw.c, x, y, z);
                     store_tile<V>(&tm_out, g, x, y, z, smem + s * TILE_BYTES);
                     bulk_commit();
                     bulk_wait_read_all();  // the store has read the slot before it is refilled
                 }
+                sw.next(g);
             }
             if (g.inject_stall) continue;  // test hook: nothing ever completes full[s]
             int x, y, z;
-            tile_origin(g, tile, x, y, z);
+            tile_origin(lw.c, x, y, z);
+            lw.next(g);
             load_tile<V>(&tm_in, g, x, y, z, smem + s * TILE_BYTES, &full[s]);
         }
         // drain: write back the slots still holding consumed tiles
@@ -821,13 +854,14 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                 continue;
             }
             const int64_t tj = int64_t(blockIdx.x) + j * gridDim.x;
-            g.partials[tj] = sum_warp_partials(red + s * (NCONS / 32));
+            g.partials[tj] = sum_warp_partials<NC>(red + s * (NC / 32));
             if (g.recon) {
                 int x, y, z;
-                tile_origin(g, tj, x, y, z);
+                tile_origin(sw.c, x, y, z);
                 store_tile<V>(&tm_out, g, x, y, z, smem + s * TILE_BYTES);
                 bulk_commit();
             }
+            sw.next(g);
         }
         bulk_wait_all();
         return;
@@ -841,33 +875,35 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
     // they must give up together; the register path has no such barrier
     constexpr bool coop = ((N >= 16) || (N == 8 && V == 1)) && V != TC_V;
     TcLane tcl;
-    uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NCONS / 32) * TC_ZS);
+    uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NC / 32) * TC_ZS);
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
     const uint32_t tczs = smem_u32(Zs + (tid >> 5) * TC_ZS);
     if constexpr (V == TC_V) {
-        if constexpr (N == 32) tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
-        else tc16_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, tid >> 5);
-        named_sync(1, NCONS);  // the table is written before any warp reads it
+        if constexpr (N == 32) tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7);
+        else tc16_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7);
+        named_sync(1, NC);  // the table is written before any warp reads it
     }
     int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it) {
+    TileWalker cw;
+    cw.init(g);
+    for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it, cw.next(g)) {
         uint8_t *buf;
         int s = 0;
         int x0 = 0, y0 = 0, z = 0, hv = 0, wv = 0;
         if (g.use_tma) {
             s = int(it % NST);
             const bool got = mbar_wait_bounded(&full[s], uint32_t((it / NST) & 1), g.timeout_ns);
-            if (coop ? named_any(3, NCONS, !got) : !got) break;
+            if (coop ? named_any(3, NC, !got) : !got) break;
             buf = smem + s * TILE_BYTES;
         } else {
             buf = smem;
-            tile_origin(g, tile, x0, y0, z);
+            tile_origin(cw.c, x0, y0, z);
             hv = min(TH, g.H - y0);
             wv = min(TW, g.W - x0);
             const uint8_t *src = g.img + int64_t(z) * g.img_stride + int64_t(y0) * g.ld + x0;
-            named_sync(1, NCONS);  // the previous tile's copy-out has read the buffer
+            named_sync(1, NC);  // the previous tile's copy-out has read the buffer
             if (al8) {
-                for (int q = tid; q < TH * (TW / 8); q += NCONS) {
+                for (int q = tid; q < TH * (TW / 8); q += NC) {
                     const int y = q / (TW / 8), x = (q - y * (TW / 8)) * 8;
                     uint2 v = make_uint2(0u, 0u);
                     if (y < hv && x + 8 <= wv) {
@@ -882,36 +918,36 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                     *reinterpret_cast<uint2 *>(buf + tile_off<V>(y, x)) = v;
                 }
             } else {
-                for (int q = tid; q < TILE_BYTES; q += NCONS) {
+                for (int q = tid; q < TILE_BYTES; q += NC) {
                     const int y = q / TW, x = q - y * TW;
                     buf[tile_off<V>(y, x)] = (y < hv && x < wv) ? src[int64_t(y) * g.ld + x] : uint8_t(0);
                 }
             }
-            named_sync(1, NCONS);
+            named_sync(1, NC);
         }
         float v;
         if constexpr (V == TC_V) {
-            if constexpr (N == 32) v = tile_tc(tcl, tctabl, g, buf, tile, tid, tczs);
-            else v = tile_tc16(tcl, tctabl, g, buf, tile, tid, tczs);
+            if constexpr (N == 32) v = tile_tc(tcl, tctabl, g, buf, cw.c, tid, tczs);
+            else v = tile_tc16(tcl, tctabl, g, buf, cw.c, tid, tczs);
         }
-        else v = process_tile<N, V>(P, g, buf, tile, tid, Ys, Zs);
+        else v = process_tile<N, V>(P, g, buf, cw.c, tid, Ys, Zs);
         if (g.use_tma) {
             // warp partial -> red[s][warp]; the producer sums the eight in order
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if ((tid & 31) == 0) red[s * (NCONS / 32) + (tid >> 5)] = v;
+            if ((tid & 31) == 0) red[s * (NC / 32) + (tid >> 5)] = v;
             if (g.recon) fence_proxy_async_smem();
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&empty[s]);
         } else {
-            const float t = reduce_consumers(v, red, tid);
+            const float t = reduce_consumers<NC>(v, red, tid);
             if (tid == 0) g.partials[tile] = t;
         }
         if (!g.use_tma && g.recon) {
-            named_sync(1, NCONS);
+            named_sync(1, NC);
             uint8_t *dst = g.recon + int64_t(z) * g.recon_stride + int64_t(y0) * g.ld_recon + x0;
             if (al8o) {
-                for (int q = tid; q < TH * (TW / 8); q += NCONS) {
+                for (int q = tid; q < TH * (TW / 8); q += NC) {
                     const int y = q / (TW / 8), x = (q - y * (TW / 8)) * 8;
                     if (y < hv && x + 8 <= wv) {
                         *reinterpret_cast<uint2 *>(dst + int64_t(y) * g.ld_recon + x) =
@@ -922,7 +958,7 @@ __global__ void __launch_bounds__(NCONS + 32, 2)
                     }
                 }
             } else {
-                for (int q = tid; q < TILE_BYTES; q += NCONS) {
+                for (int q = tid; q < TILE_BYTES; q += NC) {
                     const int y = q / TW, x = q - y * TW;
                     if (y < hv && x < wv) dst[int64_t(y) * g.ld_recon + x] = buf[tile_off<V>(y, x)];
                 }
@@ -1033,13 +1069,21 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     }
     const int dev = ensure_smem_attr(fn);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NCONS + 32, L.total);
+    const int threads = (V == TC_V ? NCONS_TC : NCONS) + 32;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, L.total);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(g.ntiles, int64_t(per_sm) * sm_count(dev));
     {
+        const int64_t per_img = int64_t(g.tiles_x) * g.tiles_y;
+        g.step_img = int(grid / per_img);
+        const int rem = int(grid - int64_t(g.step_img) * per_img);
+        g.step_ty = rem / g.tiles_x;
+        g.step_tx = rem - g.step_ty * g.tiles_x;
+    }
+    {
         const PlanK<N> &pk = plan.kparams<N>();
         void *args[] = {const_cast<PlanK<N> *>(&pk), &tin, &tout, &g};
-        const cudaError_t le = cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(NCONS + 32), args, L.total, st);
+        const cudaError_t le = cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(threads), args, L.total, st);
         if (le != cudaSuccess) {
             if (scratch) cudaFreeAsync(scratch, st);
             return cuda_fail(le, "fused kernel launch");

@@ -58,6 +58,7 @@ struct FusedGeom {
     int64_t blocks_per_img;      // (H/N) * (W/N)
     int H, W, nimg;
     int tiles_x, tiles_y;
+    int step_img, step_ty, step_tx;  // the grid stride (tiles) in (image, tile row, tile column) form
     int r, D;                    // retained coefficients, diagonal bound
     int coef_vec4;               // r % 4 == 0 and zcoef 16-byte aligned
     int use_tma;                 // tiles move by TMA (else plain loads)

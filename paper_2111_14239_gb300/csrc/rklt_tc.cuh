@@ -129,8 +129,10 @@ struct TcLane {
 };
 
 // The other per-lane constants live in a shared-memory table of TC_TAB x 32 uint4,
-// entry [k][lane] (16-byte loads by consecutive lanes hit distinct banks):
-//   k = 0, 1  I1 B of y' n-tile k: hi, lo of 2^6 T^{-1}[y'][i] (even i), then (odd i)
+// entry [k][lane] (16-byte loads by consecutive lanes hit distinct banks).  Operands
+// that an MMA takes as a register pair are stored as such (a k16 B operand whose two
+// halves are equal appears twice), so they load straight into place:
+//   k = 0, 1  I1 B of y' n-tile k: hi, hi (even i), hi, hi (odd i) of 2^6 T^{-1}[y'][i]
 //   k = 2, 3  I2 B of x' n-tile k - 2: the same for T^{-1}[x'][j]
 //   k = 4, 5  staging slots of accumulator elements q = 4 (k - 4) .. + 3: the zig-zag
 //             position when retained, else the spare slot TC_ZS - 1
@@ -138,8 +140,9 @@ struct TcLane {
 //   k = 8, 9  1.0 when retained, else 0.0
 //   k = 10, 11  F1 A fragments of k-step k - 10: T[j][x], rows j = 2g (even), 2g + 1 (odd)
 //   k = 12    F2 B: 2^-12 T[i][y] (y < 16) for i = 2g (even n-tile), then i = 2g + 1
-constexpr int TC_TAB = 13;
-constexpr int TC_TAB_BYTES = TC_TAB * 32 * 16;
+//   k = 13, 14  lo digits: I1 n-tile k - 13 (even i, odd i), then I2 n-tile k - 13
+constexpr int TC_TAB = 15;
+constexpr int TC_TAB_BYTES = 15 * 32 * 16;   // the larger of the two tables
 
 __device__ __forceinline__ float tc_T(const PlanK<32> &P, int i, int x) {
     return x < 16 ? P.T[i][x] : ((i & 1) ? -P.T[i][31 - x] : P.T[i][31 - x]);
@@ -186,13 +189,14 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
     for (int nt = 0; nt < 2; nt++) {
         const int yp = 8 * nt + g;                              // I1 n-tile column y'
         const int xp = 4 * (g >> 1) + 2 * nt + (g & 1);         // I2 n-tile column x'
-        uint4 v3, v4;
-        split_pair(s6 * P.Ti[yp][4 * t], s6 * P.Ti[yp][4 * t + 2], v3.x, v3.y);
-        split_pair(s6 * P.Ti[yp][4 * t + 1], s6 * P.Ti[yp][4 * t + 3], v3.z, v3.w);
-        split_pair(s6 * P.Ti[xp][4 * t], s6 * P.Ti[xp][4 * t + 2], v4.x, v4.y);
-        split_pair(s6 * P.Ti[xp][4 * t + 1], s6 * P.Ti[xp][4 * t + 3], v4.z, v4.w);
-        tab[nt * 32 + lane] = v3;
-        tab[(2 + nt) * 32 + lane] = v4;
+        uint32_t h3e, l3e, h3o, l3o, h4e, l4e, h4o, l4o;
+        split_pair(s6 * P.Ti[yp][4 * t], s6 * P.Ti[yp][4 * t + 2], h3e, l3e);
+        split_pair(s6 * P.Ti[yp][4 * t + 1], s6 * P.Ti[yp][4 * t + 3], h3o, l3o);
+        split_pair(s6 * P.Ti[xp][4 * t], s6 * P.Ti[xp][4 * t + 2], h4e, l4e);
+        split_pair(s6 * P.Ti[xp][4 * t + 1], s6 * P.Ti[xp][4 * t + 3], h4o, l4o);
+        tab[nt * 32 + lane] = make_uint4(h3e, h3e, h3o, h3o);
+        tab[(2 + nt) * 32 + lane] = make_uint4(h4e, h4e, h4o, h4o);
+        tab[(13 + nt) * 32 + lane] = make_uint4(l3e, l3o, l4e, l4o);
     }
     uint32_t zp[8], bs[8], kp[8];
 #pragma unroll
@@ -295,12 +299,12 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     uint32_t yh[4][2], yl[4][2];  // [group][row half]: groups y' = 0..7, 8..15, 31..24, 23..16
 #pragma unroll
     for (int nt = 0; nt < 2; nt++) {
-        const uint4 b3 = lds128(tabl + nt * 512);
+        const uint4 b3 = lds128(tabl + nt * 512), lo = lds128(tabl + (13 + nt) * 512);
         float E[4], O[4];
-        mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], b3.x, b3.x);
-        mma8(E, ch[0][0], ch[0][1], b3.y);
-        mma16(O, z4, ch[1][0], ch[1][1], cl[1][0], cl[1][1], b3.z, b3.z);
-        mma8(O, ch[1][0], ch[1][1], b3.w);
+        mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], b3.x, b3.y);
+        mma8(E, ch[0][0], ch[0][1], lo.x);
+        mma16(O, z4, ch[1][0], ch[1][1], cl[1][0], cl[1][1], b3.z, b3.w);
+        mma8(O, ch[1][0], ch[1][1], lo.y);
 #pragma unroll
         for (int p = 0; p < 2; p++) {
             const float2 e2 = make_float2(E[2 * p], E[2 * p + 1]), o2 = make_float2(O[2 * p], O[2 * p + 1]);
@@ -326,10 +330,11 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
 #pragma unroll
         for (int nt = 0; nt < 2; nt++) {
             const uint4 b4 = lds128(tabl + (2 + nt) * 512);
-            mma16(E2[nt], half4, ah0, ah1, al0, al1, b4.x, b4.x);
-            mma8(E2[nt], ah0, ah1, b4.y);
-            mma16(O2[nt], z4, oh0, oh1, ol0, ol1, b4.z, b4.z);
-            mma8(O2[nt], oh0, oh1, b4.w);
+            const uint32_t l4e = lds32(tabl + (13 + nt) * 512 + 8), l4o = lds32(tabl + (13 + nt) * 512 + 12);
+            mma16(E2[nt], half4, ah0, ah1, al0, al1, b4.x, b4.y);
+            mma8(E2[nt], ah0, ah1, l4e);
+            mma16(O2[nt], z4, oh0, oh1, ol0, ol1, b4.z, b4.w);
+            mma8(O2[nt], oh0, oh1, l4o);
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -377,25 +382,21 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     return sse2.x + sse2.y;
 }
 
-// All blocks of one tile: warp w takes block column w of both block rows.
+// The 16 blocks of one tile: warp w takes block column w of both block rows.
 __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
-                                         int64_t tile_id, int ct, uint32_t zs) {
-    const TileCoord tc = tile_coord(g, tile_id);
-    const int w = ct >> 5, lane = ct & 31;
+                                         const TileCoord &tc, int ct, uint32_t zs) {
+    const int bx = ct >> 5, lane = ct & 31;
     const int bw = g.W / 32;
     const int rows_in = min(TH / 32, (g.H - tc.ty * TH) / 32);
     const int nb_in = min(TW / 32, bw - tc.tx * (TW / 32));
-    const uint32_t t32 = smem_u32(tile);
     float sse = 0.0f;
-    if (w < nb_in) {
-        for (int by = 0; by < rows_in; by++) {
-            float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
-                                             int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + w) *
-                                                g.r
-                                : nullptr;
-            sse += tc_block32(c, tabl, t32 + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
-                              g.coef_vec4 != 0);
-        }
+    if (bx >= nb_in) return sse;
+    for (int by = 0; by < rows_in; by++) {
+        float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
+                                         int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + bx) * g.r
+                            : nullptr;
+        sse += tc_block32(c, tabl, smem_u32(tile) + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
+                          g.coef_vec4 != 0);
     }
     return sse;
 }
@@ -414,15 +415,18 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
 //       times 2^6 T^{-1}[x][j] for all 16 x, 4 adjacent x per lane
 // Row order of the lane: q = 0: y = g, 1: 16 + g, 2: 15 - g, 3: 31 - g (region rows).
 //
-// Table entries [k][lane] (uint4):
-//   k = 0   F1 A: (T[g][4t], T[g][4t+1]), (T[g][4t+2], T[g][4t+3]); F2 B for class 0
-//           and 1: 2^-12 (T[i][2t], T[i][2t+1]) with i = 2 (g & 3) + class (lanes with
-//           g >> 2 = vb carry the k-step vb's nonzero entries)
-//   k = 1   I1 B, class 0 (even i): hi, lo for column block vb3 = 0, then vb3 = 1
-//   k = 2   I1 B, class 1 (odd i)
-//   k = 3   I2 B: hi, lo of 2^6 T^{-1}[x][2t, 2t+1] for n-tile 0, then n-tile 1
-//   k = 4..5  staging slots (2 vb + hb) r + z of accumulator elements q = 4 class + e
-//   k = 6..7  2^12 s_i s_j;  k = 8..9  1.0 when retained, else 0.0
+// Table entries [k][lane] (uint4), register pairs and quads stored in place:
+//   k = 0, 1  F1 A quads of k-step 0 and 1: (P01, 0, P23, 0), (0, P01, 0, P23) with
+//             P01 = (T[g][4t], T[g][4t+1]), P23 = (T[g][4t+2], T[g][4t+3])
+//   k = 2, 3  F2 B pairs of class k - 2 for k-step vb = 0, then 1: 2^-12 (T[i][2t],
+//             T[i][2t+1]), i = 2 (g & 3) + class, nonzero only on lanes with g >> 2 = vb
+//   k = 4, 5  I1 B (hi, hi) for column block vb3 = 0, then 1; class k - 4
+//   k = 6     I1 lo digits: class 0 vb3 0, 1, class 1 vb3 0, 1
+//   k = 7     I2 B: (hi, hi) of 2^6 T^{-1}[x][2t, 2t+1] for n-tile 0, then n-tile 1
+//   k = 8     I2 lo digits for n-tile 0, 1
+//   k = 9, 10   staging slots (2 vb + hb) r + z of accumulator elements q = 4 class + e
+//   k = 11, 12  2^12 s_i s_j;  k = 13, 14  1.0 when retained, else 0.0
+constexpr int TC16_TAB = 15;
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float tc16_T(const PlanK<16> &P, int i, int x) {
     return x < 8 ? P.T[i][x] : ((i & 1) ? -P.T[i][15 - x] : P.T[i][15 - x]);
@@ -449,10 +453,18 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
     if (!write_tab) return;
     const float q12 = 1.0f / 4096.0f, s6 = 64.0f;
     const int i0 = 2 * (g & 3), i1 = 2 * (g & 3) + 1;
-    tab[0 * 32 + lane] = make_uint4(pack_h2(tc16_T(P, g, 4 * t), tc16_T(P, g, 4 * t + 1)),
-                                    pack_h2(tc16_T(P, g, 4 * t + 2), tc16_T(P, g, 4 * t + 3)),
-                                    pack_h2(q12 * P.T[i0][2 * t], q12 * P.T[i0][2 * t + 1]),
-                                    pack_h2(q12 * P.T[i1][2 * t], q12 * P.T[i1][2 * t + 1]));
+    const uint32_t p01 = pack_h2(tc16_T(P, g, 4 * t), tc16_T(P, g, 4 * t + 1));
+    const uint32_t p23 = pack_h2(tc16_T(P, g, 4 * t + 2), tc16_T(P, g, 4 * t + 3));
+    tab[0 * 32 + lane] = make_uint4(p01, 0u, p23, 0u);
+    tab[1 * 32 + lane] = make_uint4(0u, p01, 0u, p23);
+    {
+        const uint32_t b0 = pack_h2(q12 * P.T[i0][2 * t], q12 * P.T[i0][2 * t + 1]);
+        const uint32_t b1 = pack_h2(q12 * P.T[i1][2 * t], q12 * P.T[i1][2 * t + 1]);
+        const bool v0 = (g >> 2) == 0;
+        tab[2 * 32 + lane] = make_uint4(v0 ? b0 : 0u, v0 ? b0 : 0u, v0 ? 0u : b0, v0 ? 0u : b0);
+        tab[3 * 32 + lane] = make_uint4(v0 ? b1 : 0u, v0 ? b1 : 0u, v0 ? 0u : b1, v0 ? 0u : b1);
+    }
+    uint32_t l1[4];
 #pragma unroll
     for (int cls = 0; cls < 2; cls++) {
         // K index k = 2t, 2t+1 <-> D2 column (vb = t >> 1, i = 4 (t & 1) + {0, 2} + cls)
@@ -460,14 +472,19 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
         uint32_t h, l;
         split_pair(s6 * P.Ti[g][ia], s6 * P.Ti[g][ib], h, l);
         const bool v0 = (t >> 1) == 0;
-        tab[(1 + cls) * 32 + lane] = make_uint4(v0 ? h : 0u, v0 ? l : 0u, v0 ? 0u : h, v0 ? 0u : l);
+        const uint32_t h0 = v0 ? h : 0u, h1 = v0 ? 0u : h;
+        tab[(4 + cls) * 32 + lane] = make_uint4(h0, h0, h1, h1);
+        l1[2 * cls] = v0 ? l : 0u;
+        l1[2 * cls + 1] = v0 ? 0u : l;
     }
+    tab[6 * 32 + lane] = make_uint4(l1[0], l1[1], l1[2], l1[3]);
     {
-        uint4 v;
+        uint32_t ha, la, hb2, lb;
         const int xa = 4 * (g >> 1) + (g & 1), xb = xa + 2;  // n-tile 0 and 1 columns x
-        split_pair(s6 * tc16_Ti(P, xa, 2 * t), s6 * tc16_Ti(P, xa, 2 * t + 1), v.x, v.y);
-        split_pair(s6 * tc16_Ti(P, xb, 2 * t), s6 * tc16_Ti(P, xb, 2 * t + 1), v.z, v.w);
-        tab[3 * 32 + lane] = v;
+        split_pair(s6 * tc16_Ti(P, xa, 2 * t), s6 * tc16_Ti(P, xa, 2 * t + 1), ha, la);
+        split_pair(s6 * tc16_Ti(P, xb, 2 * t), s6 * tc16_Ti(P, xb, 2 * t + 1), hb2, lb);
+        tab[7 * 32 + lane] = make_uint4(ha, ha, hb2, hb2);
+        tab[8 * 32 + lane] = make_uint4(la, lb, 0u, 0u);
     }
     uint32_t zp[8], bs[8], kp[8];
 #pragma unroll
@@ -482,9 +499,9 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-        tab[(4 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
-        tab[(6 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
-        tab[(8 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
+        tab[(9 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
+        tab[(11 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
+        tab[(13 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
     }
 }
 
@@ -506,16 +523,17 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
         else sts32o<0>(a, v);
     };
     // ---- F1 (n-tiles 0..3 = rows y = g, 15 - g, 16 + g, 31 - g = lane rows q 0, 2, 1, 3)
-    const uint4 k0 = lds128(tabl);
     float d1[4][4];
     {
+        const uint4 f0 = lds128(tabl), f1 = lds128(tabl + 512);
         const float ci[4] = {c.init1[0], c.init1[0], c.init1[0], c.init1[0]};
 #pragma unroll
         for (int nt = 0; nt < 4; nt++) {
             const int q = (nt == 0) ? 0 : (nt == 1) ? 2 : (nt == 2) ? 1 : 3;
             const uint32_t w0 = ld_word(q, 0), w1 = ld_word(q, 1);
-            mma16(d1[nt], ci, k0.x, 0u, k0.y, 0u, bytes_to_biased_h2(w0, 0, 1), bytes_to_biased_h2(w0, 2, 3));
-            mma16(d1[nt], d1[nt], 0u, k0.x, 0u, k0.y, bytes_to_biased_h2(w1, 0, 1), bytes_to_biased_h2(w1, 2, 3));
+            mma16(d1[nt], ci, f0.x, f0.y, f0.z, f0.w, bytes_to_biased_h2(w0, 0, 1), bytes_to_biased_h2(w0, 2, 3));
+            mma16(d1[nt], d1[nt], f1.x, f1.y, f1.z, f1.w, bytes_to_biased_h2(w1, 0, 1),
+                  bytes_to_biased_h2(w1, 2, 3));
         }
     }
     // ---- y-parity per block row vb: S = Z[y'] + Z[15-y'], Dd = Z[y'] - Z[15-y'], digits
@@ -536,26 +554,24 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     const float z4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     float d2[2][4];
     {
-        const int vbl = (lane >> 2) >> 2;  // the k-step whose B entries this lane holds
-        const uint32_t e0 = vbl == 0 ? k0.z : 0u, e1 = vbl == 1 ? k0.z : 0u;
-        const uint32_t o0 = vbl == 0 ? k0.w : 0u, o1 = vbl == 1 ? k0.w : 0u;
-        mma16(d2[0], z4, sh[0][0], sh[0][1], sl[0][0], sl[0][1], e0, e0);
-        mma16(d2[0], d2[0], sh[1][0], sh[1][1], sl[1][0], sl[1][1], e1, e1);
-        mma16(d2[1], z4, dh[0][0], dh[0][1], dl[0][0], dl[0][1], o0, o0);
-        mma16(d2[1], d2[1], dh[1][0], dh[1][1], dl[1][0], dl[1][1], o1, o1);
+        const uint4 be = lds128(tabl + 2 * 512), bo = lds128(tabl + 3 * 512);
+        mma16(d2[0], z4, sh[0][0], sh[0][1], sl[0][0], sl[0][1], be.x, be.y);
+        mma16(d2[0], d2[0], sh[1][0], sh[1][1], sl[1][0], sl[1][1], be.z, be.w);
+        mma16(d2[1], z4, dh[0][0], dh[0][1], dl[0][0], dl[0][1], bo.x, bo.y);
+        mma16(d2[1], d2[1], dh[1][0], dh[1][1], dl[1][0], dl[1][1], bo.z, bo.w);
     }
     // ---- M: staged coefficients, zonal mask, C' digits
     uint32_t ch[2][2], cl[2][2];
 #pragma unroll
     for (int cls = 0; cls < 2; cls++) {
         if (coef) {
-            const uint4 zp = lds128(tabl + (4 + cls) * 512), bs = lds128(tabl + (6 + cls) * 512);
+            const uint4 zp = lds128(tabl + (9 + cls) * 512), bs = lds128(tabl + (11 + cls) * 512);
             sts_f32(zs + 4 * zp.x, __uint_as_float(bs.x) * d2[cls][0]);
             sts_f32(zs + 4 * zp.y, __uint_as_float(bs.y) * d2[cls][1]);
             sts_f32(zs + 4 * zp.z, __uint_as_float(bs.z) * d2[cls][2]);
             sts_f32(zs + 4 * zp.w, __uint_as_float(bs.w) * d2[cls][3]);
         }
-        const uint4 kp = lds128(tabl + (8 + cls) * 512);
+        const uint4 kp = lds128(tabl + (13 + cls) * 512);
         const float2 v0 = __fmul2_rn(make_float2(d2[cls][0], d2[cls][1]),
                                      make_float2(__uint_as_float(kp.x), __uint_as_float(kp.y)));
         const float2 v1 = __fmul2_rn(make_float2(d2[cls][2], d2[cls][3]),
@@ -566,15 +582,16 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     // ---- I1: n-tile vb3; top (y' < 8) = E + O, bottom (15 - y') = E - O
     uint32_t yh[4][2], yl[4][2];  // groups q: 0 = vb0 top, 1 = vb1 top, 2 = vb0 bottom, 3 = vb1 bottom
     {
-        const uint4 be = lds128(tabl + 1 * 512), bo = lds128(tabl + 2 * 512);
+        const uint4 be = lds128(tabl + 4 * 512), bo = lds128(tabl + 5 * 512), bl = lds128(tabl + 6 * 512);
 #pragma unroll
         for (int vb3 = 0; vb3 < 2; vb3++) {
-            const uint32_t eh = vb3 ? be.z : be.x, el = vb3 ? be.w : be.y;
-            const uint32_t oh = vb3 ? bo.z : bo.x, ol = vb3 ? bo.w : bo.y;
+            const uint32_t eh0 = vb3 ? be.z : be.x, eh1 = vb3 ? be.w : be.y;
+            const uint32_t oh0 = vb3 ? bo.z : bo.x, oh1 = vb3 ? bo.w : bo.y;
+            const uint32_t el = vb3 ? bl.y : bl.x, ol = vb3 ? bl.w : bl.z;
             float E[4], O[4];
-            mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], eh, eh);
+            mma16(E, z4, ch[0][0], ch[0][1], cl[0][0], cl[0][1], eh0, eh1);
             mma8(E, ch[0][0], ch[0][1], el);
-            mma16(O, z4, ch[1][0], ch[1][1], cl[1][0], cl[1][1], oh, oh);
+            mma16(O, z4, ch[1][0], ch[1][1], cl[1][0], cl[1][1], oh0, oh1);
             mma8(O, ch[1][0], ch[1][1], ol);
 #pragma unroll
             for (int p = 0; p < 2; p++) {
@@ -588,7 +605,7 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     // ---- I2 per (m-tile, block column hb), then error and 8-bit output.  m-tile mt has
     //      rows g (group 2 mt) and g + 8 (group 2 mt + 1): y = g, 16 + g (mt 0) and
     //      15 - g, 31 - g (mt 1); lane word x = 16 hb + 4t .. 4t + 3
-    const uint4 b4 = lds128(tabl + 3 * 512);
+    const uint4 b4 = lds128(tabl + 7 * 512), b4l = lds128(tabl + 8 * 512);
     const __half2 k10235 = __float2half2_rn(1023.5f);
     const float half4[4] = {0.5f, 0.5f, 0.5f, 0.5f};
     float2 sse2 = make_float2(0.0f, 0.0f);
@@ -599,10 +616,10 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
             const uint32_t ah0 = movm_t(yh[2 * mt][hb]), ah1 = movm_t(yh[2 * mt + 1][hb]);
             const uint32_t al0 = movm_t(yl[2 * mt][hb]), al1 = movm_t(yl[2 * mt + 1][hb]);
             float R[2][4];
-            mma16(R[0], half4, ah0, ah1, al0, al1, b4.x, b4.x);
-            mma8(R[0], ah0, ah1, b4.y);
-            mma16(R[1], half4, ah0, ah1, al0, al1, b4.z, b4.z);
-            mma8(R[1], ah0, ah1, b4.w);
+            mma16(R[0], half4, ah0, ah1, al0, al1, b4.x, b4.y);
+            mma8(R[0], ah0, ah1, b4l.x);
+            mma16(R[1], half4, ah0, ah1, al0, al1, b4.z, b4.w);
+            mma8(R[1], ah0, ah1, b4l.y);
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int q = 2 * mt + h;            // group; region row y as listed above
@@ -629,11 +646,10 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     return sse2.x + sse2.y;
 }
 
-// All regions of one tile (N = 16): warp w takes region column w of both region rows.
+// The 16 regions of one tile (N = 16): warp w takes region column w of both region rows.
 __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
-                                           int64_t tile_id, int ct, uint32_t zs) {
-    const TileCoord tc = tile_coord(g, tile_id);
-    const int w = ct >> 5, lane = ct & 31;
+                                           const TileCoord &tc, int ct, uint32_t zs) {
+    const int lane = ct & 31, w = ct >> 5;
     const int bw = g.W / 16;
     const int rows_in = min(TH / 16, (g.H - tc.ty * TH) / 16);   // block rows of the tile inside
     const int nb_in = min(TW / 16, bw - tc.tx * (TW / 16));       // block columns inside
