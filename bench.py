@@ -34,13 +34,16 @@ NIMG, SIDE = 16, 4096
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by kernel; None until a capture of the current kernel exists.
+# The fused kernel instantiation the library picks for r = N^2/8 (variant 0: one thread
+# per block; 4: tensor cores, one warp per 32 x 32 block or region).
+KERNEL = {4: "fused_kernel<4, 0>", 8: "fused_kernel<8, 0>", 16: "fused_kernel<16, 4>", 32: "fused_kernel<32, 4>"}
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
     # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
-    "fused_kernel<4>": 268512768 + 344303616,
-    "fused_kernel<8>": 268518656 + 346935552,
-    "fused_kernel<16>": 268571136 + 342560256,
-    "fused_kernel<32>": 269329920 + 356632320,
+    "fused_kernel<4, 0>": 268507136 + 343941632,
+    "fused_kernel<8, 0>": 268545024 + 347807488,
+    "fused_kernel<16, 4>": 268521984 + 338144256,
+    "fused_kernel<32, 4>": 268619520 + 342074112,
 }
 
 
@@ -62,6 +65,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.skip = 0
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
@@ -69,8 +73,15 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # the timed region starts once nvidia-smi is producing samples
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
+            self.f.flush()
+            with open(self.path) as f:
+                self.skip = sum(1 for _ in f)  # samples taken before the timed region
         except Exception:
             self.proc = None
         return self
@@ -90,18 +101,20 @@ class ClockSampler:
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for ln in f:
-                p = [x.strip() for x in ln.split(",")]
-                if len(p) < 9:
-                    continue
-                try:
-                    sm.append(float(p[1]))
-                    smax = float(p[2])
-                except ValueError:
-                    continue
-                for nm, v in zip(names, p[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+            lines = f.readlines()
+        body = lines[self.skip:] if len(lines) > self.skip else lines
+        for ln in body:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -284,7 +297,7 @@ def run_ours(args):
         r = rs[n]
         alg_bytes = NIMG * H * W * (1.0 + 4.0 * r / (n * n) + 1.0)
         gbs = alg_bytes / (kern_ms[n] / 1e3) / 1e9
-        per_n[str(n)] = {"kernel": f"fused_kernel<{n}>", "ms": round(kern_ms[n], 4), "alg_bytes": alg_bytes,
+        per_n[str(n)] = {"kernel": KERNEL[n], "ms": round(kern_ms[n], 4), "alg_bytes": alg_bytes,
                          "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4)}
     dom = max(NS, key=lambda n: kern_ms[n])
     dk = per_n[str(dom)]
@@ -447,7 +460,7 @@ def leg_serve(rk, dev, duration_s=6.0, rate=2000.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0, help="seconds of oracle work per sample")
