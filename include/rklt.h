@@ -240,7 +240,8 @@ rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, const uint8_t
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *
  * rklt_fused obtains a small per-call scratch buffer (one float per 64 x 256
- * tile) from a stream-ordered memory pool.  Some callers cannot allow that: code
+ * tile, or per 32 x 256 strip when N = 32 and the retained support stays inside
+ * i + j < 16) from a stream-ordered memory pool.  Some callers cannot allow that: code
  * running on a real-time path where an allocation may block or synchronise the
  * device, plugins whose host framework owns the whole device-memory budget and
  * leaves no room for a private pool, and callers that must keep every device
@@ -250,9 +251,9 @@ rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, const uint8_t
  * GPU that loads the library keeps until the process exits.
  *
  * Arguments, outputs and results are those of rklt_fused (bit-identical).
- * Limit: the image may span at most 65536 tiles of 64 x 256 pixels
- * (ceil(H/64) * ceil(W/256) <= 65536, e.g. 32768 x 32768); larger images are
- * rejected with RKLT_ERR_ARG before anything is enqueued.
+ * Limit: the image may span at most 65536 tiles (ceil(H/64) * ceil(W/256) <= 65536,
+ * e.g. 32768 x 32768; with 32-row strips ceil(H/32) * ceil(W/256) <= 65536); larger
+ * images are rejected with RKLT_ERR_ARG before anything is enqueued.
  * Set-up: the first call on each device, made with that device current, looks up
  * the array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  Sharing: all calls use the same array and each call
@@ -284,6 +285,16 @@ void rklt_set_wait_timeout_us(uint32_t microseconds);
  * aligned, else plain loads; 1 = plain loads always.  Results are identical;
  * the switch exists so that both transports can be tested on the same data. */
 void rklt_set_transport(int mode);
+
+/* Tensor-core engine for 32 x 32 blocks whose retained support lies inside
+ * i + j < 16 (r <= 136), for later calls from this process: 0 (default) =
+ * warp-level mma.sync with accumulators in registers; 1 = tcgen05.mma with
+ * accumulators in tensor memory (one elected thread per warp group issues the
+ * MMAs, operands staged in shared memory, 32 x 256-pixel strips).  Both compute
+ * the same exact integer stage; coefficients, reconstruction and SSE agree within
+ * the FP32 bounds of the tests (the inverse's rounding differs).  Other N and
+ * larger r are unaffected. */
+void rklt_set_tensor_engine(int mode);
 
 /* Fault injection for tests of the bounded waits: while on (non-zero), the TMA
  * producer of later fused launches issues no tile loads, so the consumers' waits

@@ -22,7 +22,7 @@ __all__ = [
     "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
     "rklt_fused", "rklt_fused_batched", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
-    "rklt_set_transport", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
+    "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
 ]
 
 STATUS = {0: "RKLT_OK", 1: "RKLT_ERR_ARG", 2: "RKLT_ERR_SHAPE", 3: "RKLT_ERR_DEGENERATE", 4: "RKLT_ERR_CUDA",
@@ -79,6 +79,7 @@ _SIGS = {
     "rklt_rsweep": (_I, [_P, _I, _P, _I, _I, _I, _L, _L, _P, _P, _P]),
     "rklt_set_wait_timeout_us": (None, [_U32]),
     "rklt_set_transport": (None, [_I]),
+    "rklt_set_tensor_engine": (None, [_I]),
     "rklt_debug_inject_stall": (None, [_I]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -330,6 +331,11 @@ def rklt_set_wait_timeout_us(us: int):
 
 def rklt_set_transport(mode: int):
     lib.rklt_set_transport(mode)
+
+
+def rklt_set_tensor_engine(mode: int):
+    """N = 32 with r <= 136: 0 warp-level mma.sync (default), 1 tcgen05 with TMEM accumulators."""
+    lib.rklt_set_tensor_engine(mode)
 
 
 def rklt_debug_inject_stall(on: bool):

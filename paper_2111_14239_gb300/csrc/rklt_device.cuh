@@ -114,6 +114,21 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
+// Wait for phase `parity` of an mbarrier by polling (for short waits such as an MMA's
+// completion), giving up after timeout_ns of GPU time like mbar_wait_bounded.
+__device__ __forceinline__ bool mbar_wait_poll(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        for (int k = 0; k < 64; k++)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > timeout_ns) {
+            atomicExch(&g_dev_status, 7u);
+            return false;
+        }
+    }
+}
+
 // Wait for phase `parity` of an mbarrier, giving up after timeout_ns of GPU
 // time; on give-up the device status latches RKLT_ERR_TIMEOUT (7).  Each retry
 // sleeps up to 0.5 ms (or the remaining limit, if shorter) unless the phase completes.

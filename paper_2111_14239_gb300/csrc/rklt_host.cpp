@@ -12,9 +12,11 @@
 namespace rklt {
 
 static std::atomic<int> g_transport{0};
+static std::atomic<int> g_tensor_engine{0};
 static std::atomic<int> g_inject_stall{0};
 
 int transport_mode() { return g_transport.load(std::memory_order_relaxed); }
+int tensor_engine() { return g_tensor_engine.load(std::memory_order_relaxed); }
 int inject_stall() { return g_inject_stall.load(std::memory_order_relaxed); }
 
 rklt_status cuda_fail(cudaError_t err, const char *what) {
@@ -95,4 +97,5 @@ bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64
 }  // namespace rklt
 
 extern "C" void rklt_set_transport(int mode) { rklt::g_transport.store(mode == 1 ? 1 : 0); }
+extern "C" void rklt_set_tensor_engine(int mode) { rklt::g_tensor_engine.store(mode == 1 ? 1 : 0); }
 extern "C" void rklt_debug_inject_stall(int on) { rklt::g_inject_stall.store(on ? 1 : 0); }

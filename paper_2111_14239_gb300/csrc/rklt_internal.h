@@ -103,11 +103,18 @@ int ensure_smem_attr(const void *kernel);     // opt in to 227 KB dynamic smem; 
 bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64_t ld, int64_t stride,
                  int box_w, int box_h, bool swizzle128 = false);
 int transport_mode();                         // 0 auto, 1 plain loads only
+int tensor_engine();                          // N = 32, D <= 16: 0 mma.sync, 1 tcgen05 / TMEM
 int inject_stall();                           // fault-injection hook for the bounded-wait test
 
 // Largest zig-zag diagonal touched by the first r coefficients, plus one:
 // every retained (i, j) has i + j < diag_bound(N, r).
 int diag_bound(int N, int r);
+
+// Whether the fused call for (N, D) runs the tensor-memory (tcgen05) kernel, and the
+// rows per tile of the kernel it runs: 32-row strips for that kernel, 64-row tiles
+// otherwise.  The fused call needs one SSE partial per tile.
+inline bool uses_tmem_kernel(int N, int D) { return N == 32 && D <= 16 && tensor_engine() == 1; }
+inline int fused_tile_rows(int N, int D) { return uses_tmem_kernel(N, D) ? 32 : kTileH; }
 
 // Device wait timeout (nanoseconds) for the next launches.
 uint64_t wait_timeout_ns();

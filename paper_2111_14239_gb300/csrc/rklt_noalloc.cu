@@ -1,6 +1,7 @@
 // rklt_noalloc.cu -- rklt_fused without any allocation.
 //
-// rklt_fused takes its per-tile SSE partials (one float per 64 x 256 tile) from
+// rklt_fused takes its per-tile SSE partials (one float per 64 x 256 tile, or per
+// 32 x 256 strip for the N = 32 tensor-memory kernel) from
 // a stream-ordered memory pool.  This variant takes them from a fixed array in
 // the library's own device memory instead, so a call performs no allocation of
 // any kind.  The array is a file-scope __device__ object: every GPU that loads
@@ -14,7 +15,7 @@
 
 namespace rklt {
 
-constexpr int64_t kNoAllocMaxTiles = 65536;  // 2^16 tiles of 64 x 256 pixels = 2^30 pixels
+constexpr int64_t kNoAllocMaxTiles = 65536;  // 2^16 tiles: 2^30 pixels (2^29 for 32-row strips)
 
 static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxTiles];
 
@@ -57,10 +58,12 @@ extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *
     if (ld < W) return fail(RKLT_ERR_SHAPE, "ld must be >= W");
     if (H > 0 && W > 0 && !d_img) return fail(RKLT_ERR_ARG, "d_img is NULL");
     if (d_recon && ld_recon < W) return fail(RKLT_ERR_SHAPE, "ld_recon must be >= W");
-    const int64_t tiles = int64_t((H + kTileH - 1) / kTileH) * ((W + kTileW - 1) / kTileW);
+    const int rows = fused_tile_rows(N, diag_bound(N, r));
+    const int64_t tiles = int64_t((H + rows - 1) / rows) * ((W + kTileW - 1) / kTileW);
     if (tiles > kNoAllocMaxTiles)
         return fail(RKLT_ERR_ARG, "image too large for rklt_fused_noalloc: it needs " + std::to_string(tiles) +
-                                      " tiles of 64 x 256 pixels and the fixed scratch array holds 65536");
+                                      " tiles of " + std::to_string(rows) +
+                                      " x 256 pixels and the fixed scratch array holds 65536");
     float *partials = nullptr;
     rklt_status st = partials_address(&partials);
     if (st != RKLT_OK) return st;

@@ -69,6 +69,20 @@ def test_noalloc_matches_fused_on_consecutive_calls(rk, n):
         assert math.isfinite(p1)
 
 
+def test_noalloc_with_tensor_memory_engine(rk):
+    """N = 32 on the tcgen05 engine tiles the image in 32-row strips (twice the
+    partials of 64-row tiles); the fixed array still gives what rklt_fused gives."""
+    plan = rk.rklt_make(32, 0.95)
+    rk.rklt_set_tensor_engine(1)
+    try:
+        for H, W, seed in ((2048, 1024, 43), (224, 800, 44)):
+            img = si.ar1_image(H, W, 0.9, seed)
+            (z0, r0, s0, p0), (z1, r1, s1, p1) = _both(rk, plan, img, 128)
+            assert np.array_equal(z1, z0) and np.array_equal(r1, r0) and s1 == s0 and p1 == p0
+    finally:
+        rk.rklt_set_tensor_engine(0)
+
+
 def test_noalloc_rejects_oversized_images(rk):
     plan = rk.rklt_make(8, 0.95)
     d = ctypes.c_void_p(256)   # never dereferenced: the size check fails first
