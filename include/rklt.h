@@ -91,6 +91,29 @@ rklt_status rklt_make_alpha(int N, double rho, double alpha, rklt_plan **out);
  * Errors: RKLT_ERR_ARG, RKLT_ERR_DEGENERATE, RKLT_ERR_OOM. */
 rklt_status rklt_make_from_matrix(int N, const int8_t *h_T, rklt_plan **out);
 
+/* Comparison transforms of the paper (Sec. 4.1, the exact KLT and the DCT rows of
+ * its results) as plans for the same pipeline: an orthonormal real N x N matrix M
+ * (rows = basis vectors) replaces T-hat, so B = M A M^T with S = I, zonal
+ * retention as for the RKLT, and A' = M^T B' M.  Built in FP64 on the host; the
+ * kernels run them in FP32 (not integer-exact).  They are accepted by rklt_fused,
+ * rklt_fused_batched, rklt_fused_noalloc, rklt_forward, rklt_zonal and
+ * rklt_inverse; rklt_forward_int, the uneven batches and rklt_rsweep reject them
+ * with RKLT_ERR_UNSUPPORTED.
+ *   rklt_make_klt: the exact KLT of the Markov-1 model with correlation rho
+ *   (Sec. 2.1, the closed form, rows with K[i][0] > 0).
+ *   rklt_make_dct: the orthonormal DCT-II, M[i][j] = c_i cos(pi (2j + 1) i / (2N)),
+ *   c_0 = sqrt(1/N), c_i = sqrt(2/N).
+ * Errors: RKLT_ERR_ARG (N, rho, out), RKLT_ERR_OOM. */
+rklt_status rklt_make_klt(int N, double rho, rklt_plan **out);
+rklt_status rklt_make_dct(int N, rklt_plan **out);
+
+/* Kind of a plan: 0 = rounded KLT (integer T), 1 = exact KLT, 2 = DCT-II; -1 for NULL. */
+int rklt_plan_kind(const rklt_plan *plan);
+
+/* The plan's analysis matrix in FP64 (h_M: N*N, row-major): T-hat = S T for a
+ * rounded plan, M for the comparison transforms.  Errors: RKLT_ERR_ARG. */
+rklt_status rklt_plan_matrix(const rklt_plan *plan, double *h_M);
+
 /* Free a plan (NULL is ignored).  Work already enqueued with it is unaffected. */
 void rklt_destroy(rklt_plan *plan);
 

@@ -15,6 +15,8 @@ Every function follows a passage of the paper (cited per function in
                                                          Table 2 are not reproduced
                                                          (parity unpinned for those rows)
   mse_to_klt, total_error_energy                      -- pinned (Table 2, RDCT reference)
+  dct_matrix                                          -- pinned (scipy's orthonormal DCT-II,
+                                                         textbook entries, orthonormality)
 """
 from __future__ import annotations
 
@@ -62,6 +64,7 @@ def _load():
         "orc_that": (None, [I, P, P, P]),
         "orc_invert": (I, [I, P, P]),
         "orc_zigzag": (None, [I, P, P]),
+        "orc_dct2": (None, [I, P]),
         "orc_int_stage": (I, [I, P, P, I, I, L, P]),
         "orc_forward": (I, [I, P, P, I, I, L, P]),
         "orc_zonal": (I, [I, P, L, I, P]),
@@ -113,6 +116,13 @@ def klt_jacobi(n: int, rho: float):
     K = np.zeros((n, n)); lam = np.zeros(n)
     _check(_load().orc_klt_jacobi(n, rho, _p(K), _p(lam)), "klt_jacobi")
     return K, lam
+
+
+def dct_matrix(n: int) -> np.ndarray:
+    """Orthonormal DCT-II, rows = basis vectors (the comparison DCT of Sec. 4.1)."""
+    M = np.zeros((n, n))
+    _load().orc_dct2(n, _p(M))
+    return M
 
 
 def round_alpha(K: np.ndarray, alpha: float):

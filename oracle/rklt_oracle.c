@@ -20,6 +20,9 @@
  *   - SSE, MSE and PSNR with peak 255                            (Sec. 4.1, Table 3)
  *   - unified coding gain, transform efficiency, MSE to the KLT and total
  *     error energy                                                (Sec. 3.1)
+ *   - the comparison transforms of the results (Sec. 4.1): the exact KLT (above)
+ *     and the orthonormal DCT-II, both run through the same per-block path with
+ *     That replaced by the transform matrix
  *
  * Readings taken where the paper is garbled or silent (each one is tested):
  *   - the closed form's sine argument is omega_i*(j - (N-1)/2) + (i+1)*pi/2
@@ -259,6 +262,18 @@ int orc_invert(int n, const double *M, double *Minv)
  * row = vertical frequency.  The walk visits the anti-diagonals d = i + j in
  * increasing order; on odd d it moves down-left (row increasing), on even d
  * up-right (row decreasing); so it starts (0,0), (0,1), (1,0), (2,0), (1,1)... */
+/* Orthonormal DCT-II (the DCT the results compare against, Sec. 4.1):
+ * M[k][j] = c_k cos(pi (2j + 1) k / (2n)), c_0 = sqrt(1/n), c_k = sqrt(2/n). */
+void orc_dct2(int n, double *M)
+{
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; k++) {
+        double c = sqrt((k == 0 ? 1.0 : 2.0) / n);
+        for (int j = 0; j < n; j++)
+            M[k * n + j] = c * cos(pi * (2 * j + 1) * k / (2.0 * n));
+    }
+}
+
 void orc_zigzag(int n, int *row, int *col)
 {
     int k = 0;

@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
-    "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
+    "rklt_make_klt", "rklt_make_dct", "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
     "rklt_fused", "rklt_fused_batched", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
@@ -60,6 +60,10 @@ _SIGS = {
     "rklt_make": (_I, [_I, _D, ctypes.POINTER(_P)]),
     "rklt_make_alpha": (_I, [_I, _D, _D, ctypes.POINTER(_P)]),
     "rklt_make_from_matrix": (_I, [_I, _P, ctypes.POINTER(_P)]),
+    "rklt_make_klt": (_I, [_I, _D, ctypes.POINTER(_P)]),
+    "rklt_make_dct": (_I, [_I, ctypes.POINTER(_P)]),
+    "rklt_plan_kind": (_I, [_P]),
+    "rklt_plan_matrix": (_I, [_P, _P]),
     "rklt_destroy": (None, [_P]),
     "rklt_plan_info": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "rklt_forward_int": (_I, [_P, _P, _I, _I, _L, _P, _P]),
@@ -138,6 +142,7 @@ class Plan:
         _check(lib.rklt_plan_info(self._h, None, None, ctypes.byref(o), ctypes.byref(n), ctypes.byref(a),
                                   ctypes.byref(rho)))
         self.N, self.alpha, self.rho, self.orthogonal = n.value, a.value, rho.value, bool(o.value)
+        self.kind = lib.rklt_plan_kind(self._h)   # 0 rounded KLT, 1 exact KLT, 2 DCT-II
 
     @property
     def handle(self):
@@ -151,6 +156,13 @@ class Plan:
         o = ctypes.c_int()
         _check(lib.rklt_plan_info(self._h, T.ctypes.data, s.ctypes.data, ctypes.byref(o), None, None, None))
         return T, s, bool(o.value)
+
+    def matrix(self):
+        """The analysis matrix (float64 [N,N]): T-hat = S T, or the exact KLT / DCT."""
+        import numpy as np
+        M = np.zeros((self.N, self.N), np.float64)
+        _check(lib.rklt_plan_matrix(self._h, M.ctypes.data))
+        return M
 
     def close(self):
         if self._h and self._h.value:
@@ -181,6 +193,20 @@ def rklt_make_from_matrix(n: int, T) -> Plan:
     T = np.ascontiguousarray(T, dtype=np.int8)
     h = ctypes.c_void_p()
     _check(lib.rklt_make_from_matrix(n, T.ctypes.data, ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def rklt_make_klt(n: int, rho: float) -> Plan:
+    """The exact KLT of the Markov-1 model as a plan (FP32 kernels, S = I)."""
+    h = ctypes.c_void_p()
+    _check(lib.rklt_make_klt(n, rho, ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def rklt_make_dct(n: int) -> Plan:
+    """The orthonormal DCT-II as a plan (FP32 kernels, S = I)."""
+    h = ctypes.c_void_p()
+    _check(lib.rklt_make_dct(n, ctypes.byref(h)))
     return Plan(h.value)
 
 
@@ -296,6 +322,13 @@ class Batch:
         t, c, g, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(lib.rklt_batch_info(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g), ctypes.byref(us)))
         return {"threads": t.value, "ctas_per_sm": c.value, "groups": g.value, "tuned_us": us.value}
+
+    def matrix(self):
+        """The analysis matrix (float64 [N,N]): T-hat = S T, or the exact KLT / DCT."""
+        import numpy as np
+        M = np.zeros((self.N, self.N), np.float64)
+        _check(lib.rklt_plan_matrix(self._h, M.ctypes.data))
+        return M
 
     def close(self):
         if self._h and self._h.value:

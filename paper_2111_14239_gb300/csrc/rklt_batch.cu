@@ -110,6 +110,7 @@ rklt_status build_groups(const rklt_item *h, int n, const rklt_plan *const *plan
     N = 0;
     for (int p = 0; p < nplans; p++) {
         if (!plans[p]) return fail(RKLT_ERR_ARG, "NULL plan");
+        if (plans[p]->p.kind != 0) return fail(RKLT_ERR_UNSUPPORTED, "uneven batches need rounded (integer) plans");
         if (N == 0) N = plans[p]->p.N;
         if (plans[p]->p.N != N) return fail(RKLT_ERR_ARG, "all plans of a batch must share N");
     }

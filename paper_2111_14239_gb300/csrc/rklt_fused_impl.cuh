@@ -672,6 +672,14 @@ __host__ __device__ inline int fused_variant(int N, int D) {
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
 
+// Variant for a real (exact KLT / DCT) plan: only the FP32 paths, since the register
+// and tensor-core paths rely on T having entries in {0, +1, -1}.
+__host__ __device__ inline int real_variant(int N, int D) {
+    if (N <= 8) return 1;
+    const int Dr = D < N ? D : N;
+    return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
+}
+
 // Consumer threads of kernel variant V.
 __host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : NCONS; }
 
@@ -679,7 +687,8 @@ template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                               int ct, float *Ys, float *Zs) {
     if constexpr (N == 4) {
-        return tile_reg<4>(P, g, tile, tc, ct);
+        if constexpr (V == 0) return tile_reg<4>(P, g, tile, tc, ct);
+        else return tile_coop<4>(P, g, tile, tc, ct, Ys, Zs);
     } else if constexpr (N == 8) {
         if constexpr (V == 0) return tile_reg<8>(P, g, tile, tc, ct);
         else return tile_coop<8>(P, g, tile, tc, ct, Ys, Zs);
@@ -760,19 +769,19 @@ struct SmemLayout {
 };
 
 template <int N>
-__host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D) {
+__host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int V) {
     SmemLayout L{};
     L.bar_off = stages * TILE_BYTES;
     L.red_off = L.bar_off + 2 * STAGES * 8;
     L.ys_off = L.red_off + STAGES * (NCONS_MAX / 32) * 4;  // barrier and reduction slots, deepest ring
     int ys = 0, zs = 0;
-    if (fused_variant(N, D) == TC_V) {
+    if (V == TC_V) {
         zs = (NCONS_TC / 32) * TC_ZS * 4 + TC_TAB_BYTES;
     } else if (N >= 16) {
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
-    } else if (N == 8 && D > REG_DMAX8) {
+    } else if (V == 1) {  // N = 4, 8 cooperative path
         ys = N * LDY * 4;
         zs = (TW / N) * r * 4;
     }
@@ -792,7 +801,7 @@ __global__ void __launch_bounds__(ncons(V) + 32, 2)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NST = g.stages;  // ring depth (<= STAGES)
-    const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D);
+    const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D, V);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *empty = full + STAGES;
     float *red = reinterpret_cast<float *>(smem + L.red_off);
@@ -873,7 +882,7 @@ __global__ void __launch_bounds__(ncons(V) + 32, 2)
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    constexpr bool coop = ((N >= 16) || (N == 8 && V == 1)) && V != TC_V;
+    constexpr bool coop = V != 0 && V != TC_V;
     TcLane tcl;
     uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NC / 32) * TC_ZS);
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
@@ -1044,7 +1053,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     };
     bool tma = !a.force_plain && is16(a.img, a.ld, g.img_stride) &&
                (!a.recon || is16(a.recon, a.ld_recon, g.recon_stride));
-    const int V = fused_variant(N, g.D);
+    const int V = plan.kind == 0 ? fused_variant(N, g.D) : real_variant(N, g.D);
     const bool swz = V == TC_V;
     const int box_w = swz ? TW / 2 : TW;
     CUtensorMap tin{}, tout{};
@@ -1056,9 +1065,10 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     }
     g.use_tma = tma ? 1 : 0;
     g.stages = swz ? 6 : ((N >= 16) ? 3 : 4);
-    const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D);
+    const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, V);
     const void *fn = nullptr;
-    if constexpr (N == 4) fn = reinterpret_cast<const void *>(fused_kernel<4, 0>);
+    if constexpr (N == 4) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<4, 0>)
+                                      : reinterpret_cast<const void *>(fused_kernel<4, 1>);
     else if constexpr (N == 8) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<8, 0>)
                                            : reinterpret_cast<const void *>(fused_kernel<8, 1>);
     else {

@@ -38,6 +38,8 @@ struct Plan {
     int N = 0;
     double rho = 0.0, alpha = 0.0;
     int orthogonal = 0;
+    int kind = 0;                // 0 rounded KLT (integer T), 1 exact KLT, 2 DCT-II (real M)
+    std::vector<double> M;       // N*N real analysis matrix (kinds 1, 2)
     std::vector<int8_t> T;       // N*N
     std::vector<double> s;       // N
     std::vector<double> Tinv;    // N*N, FP64 inverse of T
@@ -113,8 +115,10 @@ int diag_bound(int N, int r);
 // Whether the fused call for (N, D) runs the tensor-memory (tcgen05) kernel, and the
 // rows per tile of the kernel it runs: 32-row strips for that kernel, 64-row tiles
 // otherwise.  The fused call needs one SSE partial per tile.
-inline bool uses_tmem_kernel(int N, int D) { return N == 32 && D <= 16 && tensor_engine() == 1; }
-inline int fused_tile_rows(int N, int D) { return uses_tmem_kernel(N, D) ? 32 : kTileH; }
+inline bool uses_tmem_kernel(const Plan &p, int D) {
+    return p.kind == 0 && p.N == 32 && D <= 16 && tensor_engine() == 1;
+}
+inline int fused_tile_rows(const Plan &p, int D) { return uses_tmem_kernel(p, D) ? 32 : kTileH; }
 
 // Device wait timeout (nanoseconds) for the next launches.
 uint64_t wait_timeout_ns();

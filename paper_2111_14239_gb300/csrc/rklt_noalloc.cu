@@ -58,7 +58,7 @@ extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *
     if (ld < W) return fail(RKLT_ERR_SHAPE, "ld must be >= W");
     if (H > 0 && W > 0 && !d_img) return fail(RKLT_ERR_ARG, "d_img is NULL");
     if (d_recon && ld_recon < W) return fail(RKLT_ERR_SHAPE, "ld_recon must be >= W");
-    const int rows = fused_tile_rows(N, diag_bound(N, r));
+    const int rows = fused_tile_rows(plan->p, diag_bound(N, r));
     const int64_t tiles = int64_t((H + rows - 1) / rows) * ((W + kTileW - 1) / kTileW);
     if (tiles > kNoAllocMaxTiles)
         return fail(RKLT_ERR_ARG, "image too large for rklt_fused_noalloc: it needs " + std::to_string(tiles) +

@@ -113,7 +113,8 @@ void fill_kparams(Plan &p) {
     p.k.assign(sizeof(PlanK<M>), 0);
     PlanK<M> &k = *reinterpret_cast<PlanK<M> *>(p.k.data());
     for (int i = 0; i < M; i++)
-        for (int j = 0; j < M / 2; j++) k.T[i][j] = float(p.T[size_t(i) * M + j]);
+        for (int j = 0; j < M / 2; j++)
+            k.T[i][j] = p.kind == 0 ? float(p.T[size_t(i) * M + j]) : float(p.M[size_t(i) * M + j]);
     for (int l = 0; l < M / 2; l++)
         for (int j = 0; j < M; j++) {
             k.Ti[l][j] = float(p.Tinv[size_t(l) * M + j]);
@@ -123,12 +124,48 @@ void fill_kparams(Plan &p) {
         for (int j = 0; j < M; j++) k.sij[i][j] = float(p.s[i] * p.s[j]);
     for (int i = 0; i < M; i++) k.s[i] = float(p.s[i]);
     // 0, +1, -1 as binary16: 0x0000, 0x3C00, 0xBC00, duplicated into both lanes
+    // (rounded plans only; real plans never reach the binary16 kernels)
     for (int i = 0; i < M; i++)
         for (int j = 0; j < M / 2; j++) {
             const int t = p.T[size_t(i) * M + j];
             const uint32_t h = t == 0 ? 0x0000u : (t > 0 ? 0x3C00u : 0xBC00u);
             k.T2[i][j] = h | (h << 16);
         }
+}
+
+rklt_status fill_tables(Plan &p) {
+    switch (p.N) {
+        case 4: fill_kparams<4>(p); break;
+        case 8: fill_kparams<8>(p); break;
+        case 16: fill_kparams<16>(p); break;
+        case 32: fill_kparams<32>(p); break;
+        default: return fail(RKLT_ERR_ARG, "N must be 4, 8, 16 or 32");
+    }
+    return RKLT_OK;
+}
+
+// A plan for an orthonormal real matrix M (rows = basis vectors, with the row
+// parity M[i][N-1-j] = (-1)^i M[i][j] that the kernels' butterflies use): S = I,
+// inverse M^T.
+rklt_status finish_real(Plan &p) {
+    const int N = p.N;
+    p.T.assign(size_t(N) * N, 0);
+    p.s.assign(N, 1.0);
+    p.orthogonal = 1;
+    p.Tinv.assign(size_t(N) * N, 0.0);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) p.Tinv[size_t(i) * N + j] = p.M[size_t(j) * N + i];
+    return fill_tables(p);
+}
+
+// Orthonormal DCT-II: M[i][j] = c_i cos(pi (2j + 1) i / (2N)).
+std::vector<double> dct2(int N) {
+    std::vector<double> M(size_t(N) * N);
+    for (int i = 0; i < N; i++) {
+        const double c = std::sqrt((i == 0 ? 1.0 : 2.0) / N);
+        for (int j = 0; j < N; j++) M[size_t(i) * N + j] = c * std::cos(kPi * (2 * j + 1) * i / (2.0 * N));
+    }
+    return M;
 }
 
 // Validate an integer matrix and complete the plan: S (Eq. 1), T^{-1}, tables.
@@ -160,14 +197,7 @@ rklt_status finish(Plan &p) {
     std::vector<double> Td(size_t(N) * N);
     for (size_t q = 0; q < Td.size(); q++) Td[q] = p.T[q];
     if (!invert(N, Td, p.Tinv)) return fail(RKLT_ERR_DEGENERATE, "T is singular");
-    switch (N) {
-        case 4: fill_kparams<4>(p); break;
-        case 8: fill_kparams<8>(p); break;
-        case 16: fill_kparams<16>(p); break;
-        case 32: fill_kparams<32>(p); break;
-        default: return fail(RKLT_ERR_ARG, "N must be 4, 8, 16 or 32");
-    }
-    return RKLT_OK;
+    return fill_tables(p);
 }
 
 bool valid_n(int N) { return N == 4 || N == 8 || N == 16 || N == 32; }
@@ -254,6 +284,50 @@ rklt_status rklt_make_from_matrix(int N, const int8_t *h_T, rklt_plan **out) {
     rklt_status st = finish(h->p);
     if (st != RKLT_OK) { delete h; return st; }
     *out = h;
+    return RKLT_OK;
+}
+
+rklt_status rklt_make_klt(int N, double rho, rklt_plan **out) {
+    if (!out) return fail(RKLT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_n(N)) return fail(RKLT_ERR_ARG, "N must be 4, 8, 16 or 32");
+    if (!(rho > 0.0 && rho < 1.0)) return fail(RKLT_ERR_ARG, "rho must lie in (0, 1)");
+    rklt_plan *h = new (std::nothrow) rklt_plan;
+    if (!h) return fail(RKLT_ERR_OOM, "host allocation failed");
+    h->p.N = N;
+    h->p.rho = rho;
+    h->p.kind = 1;
+    h->p.M = klt(N, rho);
+    rklt_status st = finish_real(h->p);
+    if (st != RKLT_OK) { delete h; return st; }
+    *out = h;
+    return RKLT_OK;
+}
+
+rklt_status rklt_make_dct(int N, rklt_plan **out) {
+    if (!out) return fail(RKLT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_n(N)) return fail(RKLT_ERR_ARG, "N must be 4, 8, 16 or 32");
+    rklt_plan *h = new (std::nothrow) rklt_plan;
+    if (!h) return fail(RKLT_ERR_OOM, "host allocation failed");
+    h->p.N = N;
+    h->p.kind = 2;
+    h->p.M = dct2(N);
+    rklt_status st = finish_real(h->p);
+    if (st != RKLT_OK) { delete h; return st; }
+    *out = h;
+    return RKLT_OK;
+}
+
+int rklt_plan_kind(const rklt_plan *plan) { return plan ? plan->p.kind : -1; }
+
+rklt_status rklt_plan_matrix(const rklt_plan *plan, double *h_M) {
+    if (!plan || !h_M) return fail(RKLT_ERR_ARG, "plan or h_M is NULL");
+    const Plan &p = plan->p;
+    const int N = p.N;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            h_M[size_t(i) * N + j] = p.kind == 0 ? p.s[i] * p.T[size_t(i) * N + j] : p.M[size_t(i) * N + j];
     return RKLT_OK;
 }
 

@@ -173,6 +173,7 @@ extern "C" {
 rklt_status rklt_forward_int(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld, int32_t *d_C,
                              void *stream) {
     if (!plan) return fail(RKLT_ERR_ARG, "plan is NULL");
+    if (plan->p.kind != 0) return fail(RKLT_ERR_UNSUPPORTED, "the integer stage needs a rounded (integer) plan");
     rklt_status s = check_image(plan->p, d_img, H, W, ld);
     if (s) return s;
     if (H > 0 && W > 0 && !d_C) return fail(RKLT_ERR_ARG, "d_C is NULL");

@@ -233,6 +233,7 @@ extern "C" rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, co
     int N = 0;
     for (int p = 0; p < nplans; p++) {
         if (!plans[p]) return fail(RKLT_ERR_ARG, "NULL plan");
+        if (plans[p]->p.kind != 0) return fail(RKLT_ERR_UNSUPPORTED, "the r-sweep needs rounded (integer) plans");
         if (N == 0) N = plans[p]->p.N;
         if (plans[p]->p.N != N) return fail(RKLT_ERR_ARG, "all plans must share N");
     }
