@@ -310,6 +310,7 @@ def run_ours(args):
     workloads = {}
     if world == 1 and not args.no_extras:
         for name, fn in (("single_512", lambda: leg_single(rk, dev, stream)),
+                         ("comparison_klt_dct_4096", lambda: leg_comparison(rk, d_img, dev, stream)),
                          ("r_sweep_256x512", lambda: leg_sweep(rk, dev, stream)),
                          ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream)),
                          ("serving", lambda: leg_serve(rk, dev, args.serve_seconds))):
@@ -375,6 +376,30 @@ def leg_single(rk, dev, stream):
     ms = _time_ms(lambda: rk.rklt_fused(plan, img, 10, sse, ps, zcoef=zc, recon=rec, stream=stream), 200, stream)
     return {"workload": "1 x 512x512, N=8, rho=0.95, r=10, fwd+zonal+inv+PSNR", "us_per_image": ms * 1e3,
             "mpixel_per_s": 512 * 512 / (ms / 1e3) / 1e6, "psnr_db": round(float(ps.item()), 4)}
+
+
+def leg_comparison(rk, d_img, dev, stream):
+    """The paper's comparison transforms (exact KLT, DCT-II; FP32 dense) against the
+    RKLT through the same fused pass on the 16 x 4096^2 workload, N = 8, r = 8: time,
+    bandwidth and PSNR of image 0 for each."""
+    import torch
+    n, r = 8, 8
+    nimg, H, W = d_img.shape
+    nblk = (H // n) * (W // n)
+    zc = torch.empty((nimg, nblk, r), device=dev)
+    rec = torch.empty_like(d_img)
+    sse = torch.empty(nimg, dtype=torch.float64, device=dev)
+    ps = torch.empty(nimg, device=dev)
+    out = {"workload": f"{nimg} x {H}x{W} AR(1) rho={RHO}, N=8, r=8; outputs as the main line"}
+    hbm, _ = peaks()
+    for name, plan in (("rklt", rk.rklt_make(n, RHO)), ("exact_klt", rk.rklt_make_klt(n, RHO)),
+                       ("dct", rk.rklt_make_dct(n))):
+        ms = _time_ms(lambda: rk.rklt_fused_batched(plan, d_img, r, sse, ps, zcoef=zc, recon=rec, stream=stream),
+                      10, stream)
+        gbs = nimg * H * W * 2.5 / (ms / 1e3) / 1e9
+        out[name] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+                     "psnr_db_img0": round(float(ps[0].item()), 4)}
+    return out
 
 
 def leg_sweep(rk, dev, stream):
