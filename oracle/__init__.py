@@ -17,6 +17,9 @@ Every function follows a passage of the paper (cited per function in
   mse_to_klt, total_error_energy                      -- pinned (Table 2, RDCT reference)
   dct_matrix                                          -- pinned (scipy's orthonormal DCT-II,
                                                          textbook entries, orthonormality)
+  quant_pipeline                                      -- pinned (Q = R reduces to the zonal
+                                                         path; the S-absorption identity;
+                                                         hand-worked block)
 """
 from __future__ import annotations
 
@@ -65,6 +68,7 @@ def _load():
         "orc_invert": (I, [I, P, P]),
         "orc_zigzag": (None, [I, P, P]),
         "orc_dct2": (None, [I, P]),
+        "orc_quant_pipeline": (D, [I, P, P, P, P, I, I, L, I, P, P]),
         "orc_int_stage": (I, [I, P, P, I, I, L, P]),
         "orc_forward": (I, [I, P, P, I, I, L, P]),
         "orc_zonal": (I, [I, P, L, I, P]),
@@ -265,6 +269,24 @@ def pipeline(n: int, M: np.ndarray, img: np.ndarray, r: int, want_coef: bool = F
     if s < 0:
         raise ValueError(f"oracle pipeline failed ({s})")
     return float(s), zc, rc
+
+
+def quant_pipeline(n: int, T: np.ndarray, s: np.ndarray, Q: np.ndarray, img: np.ndarray, r: int,
+                   want_coef: bool = False, want_recon: bool = False):
+    """JPEG-like quantisation with S absorbed (Appendix): (sse, qcoef int32 [nblk][r] | None,
+    recon FP64 | None).  The integer decision is taken in binary32 as documented in C."""
+    img, H, W = _img(img)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    nblk = (H // n) * (W // n)
+    qc = np.zeros((nblk, r), np.int32) if want_coef else None
+    rc = np.zeros((H, W)) if want_recon else None
+    v = _load().orc_quant_pipeline(n, _p(T), _p(s), _p(Q), _p(img), H, W, W, r,
+                                   _p(qc) if qc is not None else None, _p(rc) if rc is not None else None)
+    if v < 0:
+        raise ValueError(f"oracle quant_pipeline failed ({v})")
+    return float(v), qc, rc
 
 
 def max_threads() -> int:

@@ -23,6 +23,7 @@
  *   - the comparison transforms of the results (Sec. 4.1): the exact KLT (above)
  *     and the orthonormal DCT-II, both run through the same per-block path with
  *     That replaced by the transform matrix
+ *   - JPEG-like quantisation with S absorbed into Q (Appendix)
  *
  * Readings taken where the paper is garbled or silent (each one is tested):
  *   - the closed form's sine argument is omega_i*(j - (N-1)/2) + (i+1)*pi/2
@@ -516,6 +517,66 @@ double orc_pipeline(int n, const double *M, const uint8_t *img, int H, int W, lo
     double sse = 0.0;
     for (long b = 0; b < nblk; b++) sse += blk_sse[b];
     free(blk_sse); free(Minv); free(zr); free(zc);
+    return sse;
+}
+
+/* JPEG-like quantisation with S absorbed (Appendix, Eq. bbar and the identity
+ * below it): Bbar = round(B / Q) = round(C / Qtilde) with C = T A T^T (exact
+ * integers), B = R o C, R = s s^T, Qtilde = Q / R.  round(x) = floor(x + 1/2)
+ * (the paper's rounding, Eq. 2).  The decoder dequantises B' = Bbar o Q, keeps
+ * the first r zig-zag positions, and reconstructs A' = That^{-1} B' That^{-T}.
+ *
+ * Floating point decides the integer Bbar, so this function takes that decision
+ * in binary32 exactly as specified for the kernel: w_ij = fl32(s_i s_j / Q_ij)
+ * (the FP64 quotient rounded once), q = fl32(fl32(C_ij) * w_ij), Bbar =
+ * floor(q + 1/2) (exact for |q| < 2^22).  Everything after Bbar is FP64.
+ * Outputs: qcoef_out [nblk][r] int32 (zig-zag order), recon_out H x W FP64
+ * (either may be NULL).  Returns the SSE of the FP64 reconstruction, < 0 on
+ * bad arguments. */
+double orc_quant_pipeline(int n, const int *T, const double *s, const double *Q, const uint8_t *img, int H,
+                          int W, long ld, int r, int32_t *qcoef_out, double *recon_out)
+{
+    if (!orc_shape_ok(n, H, W, ld) || r < 0 || r > n * n) return -1.0;
+    for (int k = 0; k < n * n; k++)
+        if (!(Q[k] > 0.0)) return -1.0;
+    double *That = (double *)malloc(sizeof(double) * n * n);
+    double *Tinv = (double *)malloc(sizeof(double) * n * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) That[i * n + j] = s[i] * T[i * n + j];
+    if (orc_invert(n, That, Tinv) != ORC_OK) { free(That); free(Tinv); return -2.0; }
+    float *w = (float *)malloc(sizeof(float) * n * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) w[i * n + j] = (float)(s[i] * s[j] / Q[i * n + j]);
+    int *zr = (int *)malloc(sizeof(int) * n * n), *zc = (int *)malloc(sizeof(int) * n * n);
+    orc_zigzag(n, zr, zc);
+    int bw = W / n, bh = H / n;
+    long nblk = (long)bw * bh;
+    int64_t *C = (int64_t *)malloc(sizeof(int64_t) * (nblk > 0 ? nblk : 1) * n * n);
+    orc_int_stage(n, T, img, H, W, ld, C);
+    double *Bp = (double *)malloc(sizeof(double) * n * n);
+    double *tmp = (double *)malloc(sizeof(double) * n * n);
+    double *Ar = (double *)malloc(sizeof(double) * n * n);
+    double sse = 0.0;
+    for (long b = 0; b < nblk; b++) {
+        int by = (int)(b / bw), bx = (int)(b % bw);
+        const int64_t *c = C + b * n * n;
+        for (int k = 0; k < n * n; k++) Bp[k] = 0.0;
+        for (int k = 0; k < r; k++) {
+            int i = zr[k], j = zc[k];
+            float q = (float)c[i * n + j] * w[i * n + j];
+            int32_t qb = (int32_t)floorf(q + 0.5f);
+            if (qcoef_out) qcoef_out[b * r + k] = qb;
+            Bp[i * n + j] = (double)qb * Q[i * n + j];
+        }
+        orc_block_inverse(n, Tinv, Bp, tmp, Ar);
+        for (int k = 0; k < n; k++)
+            for (int l = 0; l < n; l++) {
+                double e = (double)img[((long)by * n + k) * ld + (long)bx * n + l] - Ar[k * n + l];
+                sse += e * e;
+                if (recon_out) recon_out[((long)by * n + k) * W + (long)bx * n + l] = Ar[k * n + l];
+            }
+    }
+    free(That); free(Tinv); free(w); free(zr); free(zc); free(C); free(Bp); free(tmp); free(Ar);
     return sse;
 }
 
