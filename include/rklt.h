@@ -259,6 +259,24 @@ void rklt_batch_destroy(rklt_batch *b);
 rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, const uint8_t *d_imgs, int nimg, int H, int W,
                         int64_t ld, int64_t img_stride, double *d_sse, float *d_psnr, void *stream);
 
+/* JPEG-like quantisation with S absorbed into the quantiser (Appendix: Bbar =
+ * round(B / Q) = round(C / Qtilde) with Qtilde = Q / (s s^T) and C = T A T^T), in
+ * one pass per block: Bbar for the first r zig-zag positions, stored as int32 in
+ * d_qcoef[nimg][nblk][r] (may be NULL); the decoder's reconstruction A' = That^{-1}
+ * (Bbar o Q) That^{-T} as 8-bit output (d_recon, may be NULL) and its per-image SSE
+ * and PSNR (d_sse[nimg], d_psnr[nimg], as rklt_fused, on the unrounded A').
+ * h_Q: N*N positive finite doubles, host, row-major (caller-owned; the paper gives
+ * no Q).  round(x) = floor(x + 1/2) as in Eq. 2.  The integer decision is taken in
+ * binary32: w_ij = fl32(s_i s_j / Q_ij), q = fl32(fl32(C_ij) w_ij), Bbar =
+ * floor(q + 1/2) -- the same steps on any hardware, so Bbar is reproducible bit
+ * for bit.  Images as rklt_fused_batched (img_stride, recon_stride ignored when
+ * nimg = 1).  N in {4, 8}, rounded plans only.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED (N = 16, 32, or an
+ * exact-KLT / DCT plan), RKLT_ERR_OOM, RKLT_ERR_CUDA. */
+rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_img, int nimg, int H, int W, int64_t ld,
+                             int64_t img_stride, int r, const double *h_Q, int32_t *d_qcoef, uint8_t *d_recon,
+                             int64_t ld_recon, int64_t recon_stride, double *d_sse, float *d_psnr, void *stream);
+
 /* rklt_fused for callers that must not allocate.  (Not part of the paper: this
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *
