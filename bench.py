@@ -311,6 +311,7 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         for name, fn in (("single_512", lambda: leg_single(rk, dev, stream)),
                          ("comparison_klt_dct_4096", lambda: leg_comparison(rk, d_img, dev, stream)),
+                         ("quant_jpeg_like_4096", lambda: leg_quant(rk, d_img, dev, stream)),
                          ("r_sweep_256x512", lambda: leg_sweep(rk, dev, stream)),
                          ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream)),
                          ("serving", lambda: leg_serve(rk, dev, args.serve_seconds))):
@@ -400,6 +401,33 @@ def leg_comparison(rk, d_img, dev, stream):
         out[name] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
                      "psnr_db_img0": round(float(ps[0].item()), 4)}
     return out
+
+
+def leg_quant(rk, d_img, dev, stream):
+    """JPEG-like quantisation with S absorbed (Appendix) on the 16 x 4096^2 workload,
+    N = 8, every coefficient quantised (r = 64) with a frequency ramp Q = 2 + 3 (i + j):
+    time, bandwidth (1 B read + 4 B/coefficient int32 + 1 B reconstruction per pixel)
+    and PSNR of image 0."""
+    import numpy as np
+    import torch
+    n, r = 8, 64
+    nimg, H, W = d_img.shape
+    nblk = (H // n) * (W // n)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    Q = 2.0 + 3.0 * (i + j)
+    plan = rk.rklt_make(n, RHO)
+    qc = torch.empty(nimg * nblk * r, dtype=torch.int32, device=dev)
+    rec = torch.empty_like(d_img)
+    sse = torch.empty(nimg, dtype=torch.float64, device=dev)
+    ps = torch.empty(nimg, device=dev)
+    ms = _time_ms(lambda: rk.rklt_fused_quant(plan, d_img, r, Q, sse, ps, qcoef=qc, recon=rec, stream=stream), 10,
+                  stream)
+    bytes_px = 1.0 + 4.0 * r / (n * n) + 1.0
+    gbs = nimg * H * W * bytes_px / (ms / 1e3) / 1e9
+    hbm, _ = peaks()
+    return {"workload": f"{nimg} x {H}x{W} AR(1) rho={RHO}, N=8, r=64, Q = 2 + 3 (i + j), int32 coefficients",
+            "ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+            "bytes_per_px": bytes_px, "psnr_db_img0": round(float(ps[0].item()), 4)}
 
 
 def leg_sweep(rk, dev, stream):
