@@ -20,6 +20,9 @@ Every function follows a passage of the paper (cited per function in
   quant_pipeline                                      -- pinned (Q = R reduces to the zonal
                                                          path; the S-absorption identity;
                                                          hand-worked block)
+  mssim                                               -- pinned (identical images give 1,
+                                                         constant images' closed form,
+                                                         scipy's Gaussian filter)
 """
 from __future__ import annotations
 
@@ -69,6 +72,7 @@ def _load():
         "orc_zigzag": (None, [I, P, P]),
         "orc_dct2": (None, [I, P]),
         "orc_quant_pipeline": (D, [I, P, P, P, P, I, I, L, I, P, P]),
+        "orc_mssim": (D, [P, L, P, L, I, I, P]),
         "orc_int_stage": (I, [I, P, P, I, I, L, P]),
         "orc_forward": (I, [I, P, P, I, I, L, P]),
         "orc_zonal": (I, [I, P, L, I, P]),
@@ -287,6 +291,16 @@ def quant_pipeline(n: int, T: np.ndarray, s: np.ndarray, Q: np.ndarray, img: np.
     if v < 0:
         raise ValueError(f"oracle quant_pipeline failed ({v})")
     return float(v), qc, rc
+
+
+def mssim(x: np.ndarray, y: np.ndarray, want_map: bool = False):
+    """Mean SSIM of two uint8 images (Sec. 4.1, Wang et al.): (mssim, map | None)."""
+    x, H, W = _img(x)
+    y, H2, W2 = _img(y)
+    assert (H, W) == (H2, W2)
+    m = np.zeros((max(H - 10, 0), max(W - 10, 0))) if want_map else None
+    v = _load().orc_mssim(_p(x), W, _p(y), W, H, W, _p(m) if m is not None else None)
+    return float(v), m
 
 
 def max_threads() -> int:

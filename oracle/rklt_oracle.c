@@ -24,6 +24,7 @@
  *     and the orthonormal DCT-II, both run through the same per-block path with
  *     That replaced by the transform matrix
  *   - JPEG-like quantisation with S absorbed into Q (Appendix)
+ *   - the MSSIM quality measure of the results (Sec. 4.1)
  *
  * Readings taken where the paper is garbled or silent (each one is tested):
  *   - the closed form's sine argument is omega_i*(j - (N-1)/2) + (i+1)*pi/2
@@ -578,6 +579,54 @@ double orc_quant_pipeline(int n, const int *T, const double *s, const double *Q,
     }
     free(That); free(Tinv); free(w); free(zr); free(zc); free(C); free(Bp); free(tmp); free(Ar);
     return sse;
+}
+
+/* Mean structural similarity (MSSIM), the quality measure of Sec. 4.1 (Wang et
+ * al. 2004): for every position where an 11 x 11 window fits, with Gaussian
+ * weights w (sigma = 1.5, normalised to sum 1) over the window,
+ *   mu_x = sum w x,  sigma_x^2 = sum w (x - mu_x)^2,  sigma_xy = sum w (x - mu_x)(y - mu_y)
+ *   SSIM = (2 mu_x mu_y + C1)(2 sigma_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2))
+ * with C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2; MSSIM = the mean over the
+ * (H - 10) x (W - 10) positions.  Written as the direct definition (each window
+ * summed explicitly, deviations from the window mean), FP64.  Returns NaN when the
+ * image is smaller than the window.  map_out: (H - 10) x (W - 10) or NULL. */
+double orc_mssim(const uint8_t *x, long ldx, const uint8_t *y, long ldy, int H, int W, double *map_out)
+{
+    const int R = 5, S = 11;
+    if (H < S || W < S) return NAN;
+    double w[11][11], tot = 0.0;
+    for (int i = 0; i < S; i++)
+        for (int j = 0; j < S; j++) {
+            double di = i - R, dj = j - R;
+            w[i][j] = exp(-(di * di + dj * dj) / (2.0 * 1.5 * 1.5));
+            tot += w[i][j];
+        }
+    for (int i = 0; i < S; i++)
+        for (int j = 0; j < S; j++) w[i][j] /= tot;
+    const double C1 = (0.01 * 255.0) * (0.01 * 255.0), C2 = (0.03 * 255.0) * (0.03 * 255.0);
+    const int OH = H - S + 1, OW = W - S + 1;
+    double sum = 0.0;
+    for (int r = 0; r < OH; r++)
+        for (int c = 0; c < OW; c++) {
+            double mx = 0.0, my = 0.0;
+            for (int i = 0; i < S; i++)
+                for (int j = 0; j < S; j++) {
+                    mx += w[i][j] * x[(long)(r + i) * ldx + c + j];
+                    my += w[i][j] * y[(long)(r + i) * ldy + c + j];
+                }
+            double vx = 0.0, vy = 0.0, cxy = 0.0;
+            for (int i = 0; i < S; i++)
+                for (int j = 0; j < S; j++) {
+                    double dx = x[(long)(r + i) * ldx + c + j] - mx, dy = y[(long)(r + i) * ldy + c + j] - my;
+                    vx += w[i][j] * dx * dx;
+                    vy += w[i][j] * dy * dy;
+                    cxy += w[i][j] * dx * dy;
+                }
+            double v = (2.0 * mx * my + C1) * (2.0 * cxy + C2) / ((mx * mx + my * my + C1) * (vx + vy + C2));
+            if (map_out) map_out[(long)r * OW + c] = v;
+            sum += v;
+        }
+    return sum / ((double)OH * OW);
 }
 
 /* Number of OpenMP threads a parallel region uses (1 without OpenMP). */
