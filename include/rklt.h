@@ -277,6 +277,18 @@ rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_img, int ni
                              int64_t img_stride, int r, const double *h_Q, int32_t *d_qcoef, uint8_t *d_recon,
                              int64_t ld_recon, int64_t recon_stride, double *d_sse, float *d_psnr, void *stream);
 
+/* Mean structural similarity of two 8-bit images, the quality measure of the
+ * results (Sec. 4.1, Wang et al. 2004): 11 x 11 Gaussian window (sigma 1.5, weights
+ * normalised to sum 1), C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2, the mean of the
+ * SSIM map over the (H - 10) x (W - 10) positions where the window fits.  Typical
+ * use: d_x the original, d_y the 8-bit reconstruction of rklt_fused.  nimg images
+ * of H x W with pitches ldx, ldy and image strides (ignored for nimg = 1);
+ * d_mssim[nimg] FP64 (NaN when H or W < 11).  FP32 window sums with the values
+ * centred at 128, an FP64 mean per image in a fixed order.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_OOM, RKLT_ERR_CUDA. */
+rklt_status rklt_mssim(const uint8_t *d_x, const uint8_t *d_y, int nimg, int H, int W, int64_t ldx,
+                       int64_t x_stride, int64_t ldy, int64_t y_stride, double *d_mssim, void *stream);
+
 /* rklt_fused for callers that must not allocate.  (Not part of the paper: this
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *

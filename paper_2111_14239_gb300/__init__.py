@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
     "rklt_make_klt", "rklt_make_dct", "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
-    "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
+    "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_mssim", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
 ]
@@ -74,6 +74,7 @@ _SIGS = {
     "rklt_fused": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_fused_batched": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P]),
     "rklt_fused_quant": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _P, _L, _L, _P, _P, _P]),
+    "rklt_mssim": (_I, [_P, _P, _I, _I, _I, _L, _L, _L, _L, _P, _P]),
     "rklt_fused_noalloc": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_device_status": (_I, []),
     "rklt_fused_items": (_I, [_P, _I, _P, _I, _P, _P, _P]),
@@ -287,6 +288,16 @@ def rklt_fused_quant(plan: Plan, imgs, r: int, Q, sse, psnr, qcoef=None, recon=N
     _check(lib.rklt_fused_quant(plan.handle, imgs.data_ptr(), nimg, H, W, imgs.stride(1), imgs.stride(0), r,
                                 Qh.ctypes.data, _ptr(qcoef), _ptr(recon), ldr, rstr, _ptr(sse), _ptr(psnr),
                                 _stream(stream)))
+
+
+def rklt_mssim(x, y, out, stream=None):
+    """Mean SSIM (Sec. 4.1) of uint8 images x, y: [H, W] or [nimg, H, W]; out: float64 [nimg]."""
+    if x.dim() == 2:
+        x, y = x.unsqueeze(0), y.unsqueeze(0)
+    assert x.shape == y.shape and x.stride(2) == 1 and y.stride(2) == 1
+    nimg, H, W = x.shape
+    _check(lib.rklt_mssim(x.data_ptr(), y.data_ptr(), nimg, H, W, x.stride(1), x.stride(0), y.stride(1),
+                          y.stride(0), _ptr(out), _stream(stream)))
 
 
 def make_items(entries):
