@@ -114,6 +114,28 @@ int rklt_plan_kind(const rklt_plan *plan);
  * rounded plan, M for the comparison transforms.  Errors: RKLT_ERR_ARG. */
 rklt_status rklt_plan_matrix(const rklt_plan *plan, double *h_M);
 
+/* Algorithm 1 (Sec. 3), the design procedure of the rounded transforms, as a
+ * setup-time service on the host (FP64): for rho = step, 2 step, ..., 1 - step,
+ * T' = round(alpha K_rho) (Eq. 2, K from the closed form); each T' that differs from
+ * the one before joins the output.  h_T receives up to max_out matrices (N*N int8
+ * each, row-major), h_rho_first / h_rho_last (may be NULL) the first and last rho
+ * of the grid that produced each; *count the number of distinct matrices.  The
+ * rounded entries need not lie in {0, +1, -1} (any alpha is accepted; rklt_make
+ * checks that separately).
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_DEGENERATE (entries beyond int8),
+ * RKLT_ERR_BUDGET (more matrices than max_out; *count still holds the total). */
+rklt_status rklt_design_sweep(int N, double alpha, double step, int max_out, int8_t *h_T, double *h_rho_first,
+                              double *h_rho_last, int *count);
+
+/* Figures of merit of a plan's analysis matrix M (T-hat = S T, or the exact KLT /
+ * DCT) for the Markov-1 model with correlation rho (Sec. 3.1), host FP64; any output
+ * may be NULL:  *cg  unified coding gain 10 log10 prod_k (A_k B_k)^(-1/N) with
+ * A_k = h_k R h_k^T (h_k row k of M) and B_k = ||g_k||^2 (g_k row k of M^{-1}, as
+ * printed);  *eta transform efficiency 100 sum|r_ii| / sum|r_ij|, r = M R M^T;
+ * *mse tr((K - M) R (K - M)^T) / N;  *eps pi ||K - M||_F^2.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_DEGENERATE. */
+rklt_status rklt_figures(const rklt_plan *plan, double rho, double *cg, double *eta, double *mse, double *eps);
+
 /* Free a plan (NULL is ignored).  Work already enqueued with it is unaffected. */
 void rklt_destroy(rklt_plan *plan);
 

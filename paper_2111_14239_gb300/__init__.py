@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
-    "rklt_make_klt", "rklt_make_dct", "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
+    "rklt_make_klt", "rklt_make_dct", "rklt_design_sweep", "rklt_figures", "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
     "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_mssim", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
@@ -64,6 +64,8 @@ _SIGS = {
     "rklt_make_dct": (_I, [_I, ctypes.POINTER(_P)]),
     "rklt_plan_kind": (_I, [_P]),
     "rklt_plan_matrix": (_I, [_P, _P]),
+    "rklt_design_sweep": (_I, [_I, _D, _D, _I, _P, _P, _P, ctypes.POINTER(_I)]),
+    "rklt_figures": (_I, [_P, _D, _P, _P, _P, _P]),
     "rklt_destroy": (None, [_P]),
     "rklt_plan_info": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "rklt_forward_int": (_I, [_P, _P, _I, _I, _L, _P, _P]),
@@ -210,6 +212,25 @@ def rklt_make_dct(n: int) -> Plan:
     h = ctypes.c_void_p()
     _check(lib.rklt_make_dct(n, ctypes.byref(h)))
     return Plan(h.value)
+
+
+def rklt_design_sweep(n: int, alpha: float, step: float, max_out: int = 64):
+    """Algorithm 1 (Sec. 3): list of (T int8 [N,N], rho_first, rho_last)."""
+    import numpy as np
+    T = np.zeros((max_out, n, n), np.int8)
+    lo = np.zeros(max_out)
+    hi = np.zeros(max_out)
+    cnt = ctypes.c_int()
+    _check(lib.rklt_design_sweep(n, alpha, step, max_out, T.ctypes.data, lo.ctypes.data, hi.ctypes.data,
+                                 ctypes.byref(cnt)))
+    return [(T[k].copy(), float(lo[k]), float(hi[k])) for k in range(cnt.value)]
+
+
+def rklt_figures(plan: Plan, rho: float) -> dict:
+    """Figures of merit of the plan's matrix for the Markov-1 model (Sec. 3.1)."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib.rklt_figures(plan.handle, rho, *[ctypes.byref(x) for x in v]))
+    return dict(cg=v[0].value, eta=v[1].value, mse=v[2].value, eps=v[3].value)
 
 
 def rklt_plan_info(plan: Plan):

@@ -321,6 +321,100 @@ rklt_status rklt_make_dct(int N, rklt_plan **out) {
 
 int rklt_plan_kind(const rklt_plan *plan) { return plan ? plan->p.kind : -1; }
 
+// Algorithm 1 (Sec. 3): for rho = step, 2 step, ..., 1 - step, T' = round(alpha K_rho)
+// (Eq. 2); every T' that differs from the previous one joins the output set.
+rklt_status rklt_design_sweep(int N, double alpha, double step, int max_out, int8_t *h_T, double *h_rho_first,
+                              double *h_rho_last, int *count) {
+    if (!count) return fail(RKLT_ERR_ARG, "count is NULL");
+    *count = 0;
+    if (!valid_n(N)) return fail(RKLT_ERR_ARG, "N must be 4, 8, 16 or 32");
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(RKLT_ERR_ARG, "alpha must be positive");
+    if (!(step > 0.0 && step < 0.5)) return fail(RKLT_ERR_ARG, "step must lie in (0, 0.5)");
+    if (max_out < 0 || (max_out > 0 && !h_T)) return fail(RKLT_ERR_ARG, "h_T is NULL");
+    std::vector<int8_t> prev;
+    const long steps = std::lround(1.0 / step);
+    int n = 0;
+    for (long k = 1; k < steps; k++) {
+        const double rho = k * step;
+        const std::vector<double> K = klt(N, rho);
+        std::vector<int8_t> T(K.size());
+        for (size_t q = 0; q < K.size(); q++) {
+            const double t = std::floor(alpha * K[q] + 0.5);
+            if (t < -127.0 || t > 127.0) return fail(RKLT_ERR_DEGENERATE, "round(alpha*K) leaves the int8 range");
+            T[q] = int8_t(t);
+        }
+        if (T != prev) {
+            if (n < max_out) {
+                std::memcpy(h_T + size_t(n) * N * N, T.data(), T.size());
+                if (h_rho_first) h_rho_first[n] = rho;
+            }
+            n++;
+            prev = T;
+        }
+        if (n <= max_out && h_rho_last) h_rho_last[n - 1] = rho;
+    }
+    *count = n;
+    return n > max_out ? fail(RKLT_ERR_BUDGET, "more distinct matrices than max_out; *count holds the total")
+                       : RKLT_OK;
+}
+
+// Figures of merit of a plan's analysis matrix M (T-hat, or the exact KLT / DCT)
+// for the Markov-1 model with correlation rho (Sec. 3.1): unified coding gain, transform
+// efficiency, MSE to the exact KLT and total error energy.
+rklt_status rklt_figures(const rklt_plan *plan, double rho, double *cg, double *eta, double *mse, double *eps) {
+    if (!plan) return fail(RKLT_ERR_ARG, "plan is NULL");
+    if (!(rho > 0.0 && rho < 1.0)) return fail(RKLT_ERR_ARG, "rho must lie in (0, 1)");
+    const Plan &p = plan->p;
+    const int N = p.N;
+    std::vector<double> M(size_t(N) * N), Minv;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            M[size_t(i) * N + j] = p.kind == 0 ? p.s[i] * p.T[size_t(i) * N + j] : p.M[size_t(i) * N + j];
+    if (!invert(N, M, Minv)) return fail(RKLT_ERR_DEGENERATE, "the analysis matrix is singular");
+    std::vector<double> R(size_t(N) * N);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) R[size_t(i) * N + j] = std::pow(rho, std::abs(i - j));
+    const std::vector<double> K = klt(N, rho);
+    if (cg) {  // 10 log10 prod_k (A_k B_k)^(-1/N), A_k = h_k R h_k^T, B_k = ||row k of M^{-1}||^2
+        double acc = 0.0;
+        for (int k = 0; k < N; k++) {
+            double A = 0.0, B = 0.0;
+            for (int i = 0; i < N; i++)
+                for (int j = 0; j < N; j++) A += M[size_t(k) * N + i] * M[size_t(k) * N + j] * R[size_t(i) * N + j];
+            for (int j = 0; j < N; j++) B += Minv[size_t(k) * N + j] * Minv[size_t(k) * N + j];
+            acc += std::log10(A * B);
+        }
+        *cg = -10.0 * acc / N;
+    }
+    if (eta) {  // 100 sum |r_ii| / sum |r_ij|, r = M R M^T
+        double diag = 0.0, all = 0.0;
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++) {
+                double r = 0.0;
+                for (int a = 0; a < N; a++)
+                    for (int b = 0; b < N; b++) r += M[size_t(i) * N + a] * R[size_t(a) * N + b] * M[size_t(j) * N + b];
+                all += std::fabs(r);
+                if (i == j) diag += std::fabs(r);
+            }
+        *eta = 100.0 * diag / all;
+    }
+    if (mse) {  // tr((K - M) R (K - M)^T) / N
+        double tr = 0.0;
+        for (int i = 0; i < N; i++)
+            for (int a = 0; a < N; a++)
+                for (int b = 0; b < N; b++)
+                    tr += (K[size_t(i) * N + a] - M[size_t(i) * N + a]) * R[size_t(a) * N + b] *
+                          (K[size_t(i) * N + b] - M[size_t(i) * N + b]);
+        *mse = tr / N;
+    }
+    if (eps) {  // pi ||K - M||_F^2
+        double f = 0.0;
+        for (size_t q = 0; q < M.size(); q++) f += (K[q] - M[q]) * (K[q] - M[q]);
+        *eps = kPi * f;
+    }
+    return RKLT_OK;
+}
+
 rklt_status rklt_plan_matrix(const rklt_plan *plan, double *h_M) {
     if (!plan || !h_M) return fail(RKLT_ERR_ARG, "plan or h_M is NULL");
     const Plan &p = plan->p;
