@@ -431,6 +431,12 @@ def leg_quant(rk, d_img, dev, stream):
             "bytes_per_px": bytes_px, "psnr_db_img0": round(float(ps[0].item()), 4)}
 
 
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """FP32 FMA peak from the unit counts and the maximum SM clock (GB300: 152 SMs x
+    128 lanes)."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def leg_mssim(rk, d_img, dev, stream):
     """MSSIM (Sec. 4.1) of the 16 x 4096^2 originals against their 8-bit RKLT
     reconstructions (N = 8, r = 8): time of the MSSIM pass alone (2 B/px read) and
@@ -447,8 +453,16 @@ def leg_mssim(rk, d_img, dev, stream):
     ms = _time_ms(lambda: rk.rklt_mssim(d_img, rec, out, stream=stream), 10, stream)
     gbs = nimg * H * W * 2.0 / (ms / 1e3) / 1e9
     hbm, _ = peaks()
+    # ALU roofline: the separable window costs 4 sums x (11 + 11) taps x 2 flop = 176
+    # FP32 flop per output position; peak = 152 SMs x 128 FP32 lanes x 2 flop x SM clock
+    npos = nimg * (H - 10) * (W - 10)
+    tflops = npos * 176.0 / (ms / 1e3) / 1e12
+    fp32_peak = fp32_peak_tflops()
     return {"workload": f"{nimg} x {H}x{W}: original vs 8-bit RKLT reconstruction (N=8, r=8)",
             "ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+            "roofline": {"bound": "alu", "achieved": round(tflops, 2), "peak": round(fp32_peak, 1),
+                         "unit": "TFLOP/s", "frac": round(tflops / fp32_peak, 4),
+                         "flop_per_position": 176, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
             "mssim_img0": round(float(out[0].item()), 6), "psnr_db_img0": round(float(ps[0].item()), 4)}
 
 

@@ -69,7 +69,8 @@ rklt_status rklt_fused(const rklt_plan *plan, const uint8_t *d_img, int H, int W
 rklt_status rklt_device_status(void) {
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    unsigned int v = take_status_n4() | take_status_n8() | take_status_n16() | take_status_n32() | take_status_split();
+    unsigned int v = take_status_n4() | take_status_n8() | take_status_n16() | take_status_n32() | take_status_split() |
+                     take_status_mssim();
     if (v) return fail(RKLT_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return RKLT_OK;
 }

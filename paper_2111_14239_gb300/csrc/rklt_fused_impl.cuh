@@ -22,15 +22,20 @@
 // consumers copy each tile in and out with plain vector loads.  Both modes run the
 // same per-block code in the same order, so their results are identical.
 //
+// JPEG-like quantisation (N = 4, 8; Appendix): the same kernels with the
+// retained C quantised in place, Bbar = floor(fl32(C w) + 1/2) with
+// w = fl32(s_i s_j / Q_ij), written as int32 where the coefficients go, and the
+// inverse run on the dequantised Bbar o Qtilde (Qtilde = Q / (s s^T)).
+//
 // Work split inside a tile:
 //   register path  (N = 4, and N = 8 with D <= 5): one thread owns a whole block;
 //   tensor-core path (N = 32 with D <= 16, rklt_tc.cuh): one warp owns a block and
 //     runs every contraction as fp16 mma.sync; tiles then arrive as two 128-byte
 //     swizzled halves;
-//   cooperative path (N = 16, N = 32 with D > 16, and N = 8 with D > 5): per
-//     block-row of the tile, threads own columns for the column passes and
-//     (block, row) pairs for the row passes, exchanging through a padded
-//     shared-memory buffer.
+//   cooperative path (N = 16, N = 32 with D > 16, N = 8 with D > 5, and exact-KLT /
+//     DCT plans): threads own columns for the column passes and (block, row) pairs
+//     for the row passes, exchanging through a padded shared-memory buffer (all
+//     block-rows of a tile at once for N >= 8; block-row by block-row for N = 4).
 #pragma once
 
 #include <cudaTypedefs.h>
@@ -54,6 +59,14 @@ constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchang
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
 constexpr int REG_DMAX8 = 5;     // N = 8: register path up to this diagonal bound
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
+constexpr int QV = 8;            // added to a variant number (N = 4, 8): quantised coefficients
+__host__ __device__ constexpr int vbase(int V) { return V & 7; }
+
+// The quantiser's integer decision for one retained C (binary32, no contraction).
+template <int N>
+__device__ __forceinline__ float quant_code(const PlanK<N> &P, int i, int j, float c) {
+    return floorf(__fadd_rn(__fmul_rn(c, P.qw[i][j]), 0.5f));
+}
 
 // ---------------------------------------------------------------------------
 // Register path: one N x N block per thread.  D is a compile-time constant.
@@ -82,7 +95,7 @@ __device__ __forceinline__ void load_block_words(const uint8_t *src, int64_t ld,
 
 // The whole per-block computation on a block held in registers (w); the 8-bit
 // reconstruction is written to dst (row stride ldd bytes) when recon is set.
-template <int N, int D>
+template <int N, int D, bool Q = false>
 __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&w)[N][N / 4], uint8_t *dst,
                                             int64_t ldd, int r, float *coef, bool vec4, bool recon) {
     constexpr int H2 = N / 2;
@@ -115,7 +128,9 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
         }
     }
     // row transform: C = Y T^T on the support i + j < D; zonal mask on the last diagonal
+    // (quantised: Bq = Bbar as exact FP32 integers, Cm = Bbar o Qtilde)
     float Cm[DA][DA];
+    [[maybe_unused]] float Bq[Q ? DA : 1][Q ? DA : 1];
 #pragma unroll
     for (int i = 0; i < DR; i++) {
         float s[H2], d[H2];
@@ -130,8 +145,14 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
                 float acc = 0.0f;
 #pragma unroll
                 for (int l = 0; l < H2; l++) acc = fmaf(P.T[j][l], (j & 1) ? d[l] : s[l], acc);
-                if (i + j == D - 1) acc = (zz_index(N, i, j) < r) ? acc : 0.0f;
-                Cm[i][j] = acc;
+                const bool keep = i + j < D - 1 || zz_index(N, i, j) < r;
+                if constexpr (Q) {
+                    const float bq = keep ? quant_code<N>(P, i, j, acc) : 0.0f;
+                    Bq[i][j] = bq;
+                    Cm[i][j] = bq * P.qt[i][j];
+                } else {
+                    Cm[i][j] = keep ? acc : 0.0f;
+                }
             }
         }
     }
@@ -145,7 +166,8 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         const int k = 4 * k4 + q, i = zz_row(N, k), j = zz_col(N, k);
-                        v[q] = (i + j < D) ? P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0] : 0.0f;
+                        if constexpr (Q) v[q] = (i + j < D) ? __int_as_float(int(Bq[i < DA ? i : 0][j < DA ? j : 0])) : 0.0f;
+                        else v[q] = (i + j < D) ? P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0] : 0.0f;
                     }
                     *reinterpret_cast<float4 *>(coef + 4 * k4) = make_float4(v[0], v[1], v[2], v[3]);
                 }
@@ -154,7 +176,10 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 #pragma unroll
             for (int k = 0; k < N * N; k++) {
                 const int i = zz_row(N, k), j = zz_col(N, k);
-                if (i + j < D && k < r) coef[k] = P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0];
+                if (i + j < D && k < r) {
+                    if constexpr (Q) coef[k] = __int_as_float(int(Bq[i < DA ? i : 0][j < DA ? j : 0]));
+                    else coef[k] = P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0];
+                }
             }
         }
     }
@@ -227,36 +252,36 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 }
 
 // One block of a shared-memory tile, transformed in place.
-template <int N, int D>
+template <int N, int D, bool Q>
 __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
                                            bool recon) {
     uint32_t w[N][N / 4];
     load_block_words<N>(blk, TW, w);
-    return block_core<N, D>(P, w, blk, TW, r, coef, vec4, recon);
+    return block_core<N, D, Q>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
-template <int N>
+template <int N, bool Q>
 __device__ __forceinline__ float block_reg_dispatch(const PlanK<N> &P, uint8_t *blk, int D, int r, float *coef,
                                                     bool vec4, bool recon) {
     if constexpr (N == 4) {
         switch (D) {
-            case 0: return block_reg<4, 0>(P, blk, r, coef, vec4, recon);
-            case 1: return block_reg<4, 1>(P, blk, r, coef, vec4, recon);
-            case 2: return block_reg<4, 2>(P, blk, r, coef, vec4, recon);
-            case 3: return block_reg<4, 3>(P, blk, r, coef, vec4, recon);
-            case 4: return block_reg<4, 4>(P, blk, r, coef, vec4, recon);
-            case 5: return block_reg<4, 5>(P, blk, r, coef, vec4, recon);
-            case 6: return block_reg<4, 6>(P, blk, r, coef, vec4, recon);
-            default: return block_reg<4, 7>(P, blk, r, coef, vec4, recon);
+            case 0: return block_reg<4, 0, Q>(P, blk, r, coef, vec4, recon);
+            case 1: return block_reg<4, 1, Q>(P, blk, r, coef, vec4, recon);
+            case 2: return block_reg<4, 2, Q>(P, blk, r, coef, vec4, recon);
+            case 3: return block_reg<4, 3, Q>(P, blk, r, coef, vec4, recon);
+            case 4: return block_reg<4, 4, Q>(P, blk, r, coef, vec4, recon);
+            case 5: return block_reg<4, 5, Q>(P, blk, r, coef, vec4, recon);
+            case 6: return block_reg<4, 6, Q>(P, blk, r, coef, vec4, recon);
+            default: return block_reg<4, 7, Q>(P, blk, r, coef, vec4, recon);
         }
     } else {
         switch (D) {
-            case 0: return block_reg<N, 0>(P, blk, r, coef, vec4, recon);
-            case 1: return block_reg<N, 1>(P, blk, r, coef, vec4, recon);
-            case 2: return block_reg<N, 2>(P, blk, r, coef, vec4, recon);
-            case 3: return block_reg<N, 3>(P, blk, r, coef, vec4, recon);
-            case 4: return block_reg<N, 4>(P, blk, r, coef, vec4, recon);
-            default: return block_reg<N, 5>(P, blk, r, coef, vec4, recon);
+            case 0: return block_reg<N, 0, Q>(P, blk, r, coef, vec4, recon);
+            case 1: return block_reg<N, 1, Q>(P, blk, r, coef, vec4, recon);
+            case 2: return block_reg<N, 2, Q>(P, blk, r, coef, vec4, recon);
+            case 3: return block_reg<N, 3, Q>(P, blk, r, coef, vec4, recon);
+            case 4: return block_reg<N, 4, Q>(P, blk, r, coef, vec4, recon);
+            default: return block_reg<N, 5, Q>(P, blk, r, coef, vec4, recon);
         }
     }
 }
@@ -299,7 +324,7 @@ struct TileWalker {
     }
 };
 
-template <int N>
+template <int N, bool Q>
 __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
@@ -312,7 +337,7 @@ __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g,
         if (gy * N >= g.H || gx * N >= g.W) continue;
         float *coef = nullptr;
         if (g.zcoef) coef = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(gy) * bw + gx) * g.r;
-        sse += block_reg_dispatch<N>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
+        sse += block_reg_dispatch<N, Q>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
                                      g.recon != nullptr);
     }
     return sse;
@@ -325,7 +350,7 @@ __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g,
 // patterns).  Coefficients are staged in Zs in zig-zag order and written out
 // contiguously.  D and r are runtime values.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, bool Q>
 __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                            int ct, float *Ys, float *Zs) {
     constexpr int H2 = N / 2;
@@ -386,8 +411,15 @@ __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g
 #pragma unroll
                         for (int l = 0; l < H2; l++) acc = fmaf(P.T[j][l], (j & 1) ? d[l] : s[l], acc);
                         const int z = zz_index(N, i, j);
-                        const float c = (z < r) ? acc : 0.0f;
-                        if (z < r) Zs[b * r + z] = (si * P.s[j]) * c;
+                        float c;
+                        if constexpr (Q) {
+                            const float bq = (z < r) ? quant_code<N>(P, i, j, acc) : 0.0f;
+                            if (z < r) Zs[b * r + z] = __int_as_float(int(bq));
+                            c = bq * P.qt[i][j];
+                        } else {
+                            c = (z < r) ? acc : 0.0f;
+                            if (z < r) Zs[b * r + z] = (si * P.s[j]) * c;
+                        }
 #pragma unroll
                         for (int l = 0; l < H2; l++) {
                             if (j & 1) xo[l] = fmaf(c, P.Ti[l][j], xo[l]);
@@ -445,7 +477,7 @@ __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g
 }
 
 // ---------------------------------------------------------------------------
-// Cooperative path for N = 16 and 32.  All block-rows of the tile (R = 64/N of
+// Cooperative path for N = 8, 16 and 32.  All block-rows of the tile (R = 64/N of
 // them, NB = 256/N blocks each) are transformed together in three phases
 // separated by barriers:
 //   1. column pass: a thread takes two adjacent columns of one block-row and forms
@@ -463,11 +495,13 @@ __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g
 template <int N>
 __host__ __device__ constexpr int coop2_rounds() { return TH / N; }
 
+// Whether the coefficients are staged in shared memory (then written out
+// contiguously per block-row) rather than stored from the row pass directly.
 __host__ __device__ inline bool coop2_stage_coef(int N, int r) {
-    return int64_t(TH / N) * (TW / N) * (r | 1) * 4 <= 32 * 1024;
+    return int64_t(TH / N) * (TW / N) * (r | 1) * 4 <= (N == 8 ? 72 : 32) * 1024;
 }
 
-template <int N, int DRM>
+template <int N, int DRM, bool Q = false>
 __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct, float *Ys, float *Zs) {
     constexpr int H2 = N / 2;
@@ -557,9 +591,16 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
                 for (int l = 0; l < H2; l++) acc = fmaf(P.T[j][l], (j & 1) ? d[l] : s[l], acc);
                 const int z = zz_index(N, i, j);
                 const bool keep = z < r;
-                const float c = keep ? acc : 0.0f;
+                float c, bval;
+                if constexpr (Q) {
+                    const float bq = keep ? quant_code<N>(P, i, j, acc) : 0.0f;
+                    c = bq * P.qt[i][j];
+                    bval = __int_as_float(int(bq));
+                } else {
+                    c = keep ? acc : 0.0f;
+                    bval = (si * P.s[j]) * c;
+                }
                 if (keep) {
-                    const float bval = (si * P.s[j]) * c;
                     if (stage) zs[z] = bval;
                     else if (zg) zg[z] = bval;
                 }
@@ -660,12 +701,15 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
 namespace rklt {
 
 // Kernel variant V (picked on the host from the diagonal bound D):
-//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), 1 cooperative;
+//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), else 3;
 //   N = 32 with D <= 16, N = 16 with D <= 8: TC_V (tensor cores);
-//   N >= 16 otherwise: 1, 2, 3 = cooperative path sized for Dr <= N/4, N/2, N.
+//   N >= 16 otherwise: 1, 2, 3 = cooperative path (all block-rows at once) sized for
+//   Dr <= N/4, N/2, N;  N = 8: 2, 3 = the same path sized for Dr <= 4, 8;
+//   N = 4: 1 = cooperative path block-row by block-row.
+// QV is added for the quantised form (N = 4, 8).
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
-    if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
+    if (N == 8) return D <= REG_DMAX8 ? 0 : 3;
     if (N == 32 && D <= TC_DMAX) return TC_V;
     if (N == 16 && D <= TC_DMAX16) return TC_V;
     const int Dr = D < N ? D : N;
@@ -675,7 +719,8 @@ __host__ __device__ inline int fused_variant(int N, int D) {
 // Variant for a real (exact KLT / DCT) plan: only the FP32 paths, since the register
 // and tensor-core paths rely on T having entries in {0, +1, -1}.
 __host__ __device__ inline int real_variant(int N, int D) {
-    if (N <= 8) return 1;
+    if (N == 4) return 1;
+    if (N == 8) return D <= 4 ? 2 : 3;
     const int Dr = D < N ? D : N;
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
@@ -686,12 +731,13 @@ __host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : N
 template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                               int ct, float *Ys, float *Zs) {
-    if constexpr (N == 4) {
-        if constexpr (V == 0) return tile_reg<4>(P, g, tile, tc, ct);
-        else return tile_coop<4>(P, g, tile, tc, ct, Ys, Zs);
-    } else if constexpr (N == 8) {
-        if constexpr (V == 0) return tile_reg<8>(P, g, tile, tc, ct);
-        else return tile_coop<8>(P, g, tile, tc, ct, Ys, Zs);
+    if constexpr (N == 4 || N == 8) {
+        constexpr bool Q = V >= QV;
+        constexpr int VB = vbase(V);
+        if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
+        else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
+        else if constexpr (N == 8 && VB == 3) return tile_coop2<8, 8, Q>(P, g, tile, tc, ct, Ys, Zs);
+        else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
         if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tc, ct, Ys, Zs);
         else if constexpr (V == 2) return tile_coop2<N, N / 2>(P, g, tile, tc, ct, Ys, Zs);
@@ -777,11 +823,11 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int 
     int ys = 0, zs = 0;
     if (V == TC_V) {
         zs = (NCONS_TC / 32) * TC_ZS * 4 + TC_TAB_BYTES;
-    } else if (N >= 16) {
+    } else if (N >= 16 || V >= 2) {  // all block-rows at once
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
-    } else if (V == 1) {  // N = 4, 8 cooperative path
+    } else if (V == 1) {  // N = 4, 8 cooperative path, block-row by block-row
         ys = N * LDY * 4;
         zs = (TW / N) * r * 4;
     }
@@ -801,7 +847,7 @@ __global__ void __launch_bounds__(ncons(V) + 32, 2)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NST = g.stages;  // ring depth (<= STAGES)
-    const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D, V);
+    const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D, vbase(V));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *empty = full + STAGES;
     float *red = reinterpret_cast<float *>(smem + L.red_off);
@@ -882,7 +928,7 @@ __global__ void __launch_bounds__(ncons(V) + 32, 2)
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    constexpr bool coop = V != 0 && V != TC_V;
+    constexpr bool coop = vbase(V) != 0 && V != TC_V;
     TcLane tcl;
     uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NC / 32) * TC_ZS);
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
@@ -1053,7 +1099,22 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     };
     bool tma = !a.force_plain && is16(a.img, a.ld, g.img_stride) &&
                (!a.recon || is16(a.recon, a.ld_recon, g.recon_stride));
-    const int V = plan.kind == 0 ? fused_variant(N, g.D) : real_variant(N, g.D);
+    int V = plan.kind == 0 ? fused_variant(N, g.D) : real_variant(N, g.D);
+    // quantised call: the plan's constants plus this call's quantiser tables
+    PlanK<N> pq;
+    const PlanK<N> *pk = &plan.kparams<N>();
+    if constexpr (N <= 8) {
+        if (a.Q) {
+            V += QV;
+            pq = *pk;
+            for (int i = 0; i < N; i++)
+                for (int j = 0; j < N; j++) {
+                    pq.qw[i][j] = float(plan.s[i] * plan.s[j] / a.Q[i * N + j]);
+                    pq.qt[i][j] = float(a.Q[i * N + j] / (plan.s[i] * plan.s[j]));
+                }
+            pk = &pq;
+        }
+    }
     const bool swz = V == TC_V;
     const int box_w = swz ? TW / 2 : TW;
     CUtensorMap tin{}, tout{};
@@ -1064,14 +1125,24 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    g.stages = swz ? 6 : ((N >= 16) ? 3 : 4);
-    const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, V);
+    g.stages = swz ? 6 : ((N >= 16 || vbase(V) >= 2) ? 3 : 4);
+    const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, vbase(V));
     const void *fn = nullptr;
-    if constexpr (N == 4) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<4, 0>)
-                                      : reinterpret_cast<const void *>(fused_kernel<4, 1>);
-    else if constexpr (N == 8) fn = V == 0 ? reinterpret_cast<const void *>(fused_kernel<8, 0>)
-                                           : reinterpret_cast<const void *>(fused_kernel<8, 1>);
-    else {
+    if constexpr (N == 4) {
+        switch (V) {
+            case 0: fn = reinterpret_cast<const void *>(fused_kernel<4, 0>); break;
+            case 1: fn = reinterpret_cast<const void *>(fused_kernel<4, 1>); break;
+            default: fn = reinterpret_cast<const void *>(fused_kernel<4, QV>); break;
+        }
+    } else if constexpr (N == 8) {
+        switch (V) {
+            case 0: fn = reinterpret_cast<const void *>(fused_kernel<8, 0>); break;
+            case 2: fn = reinterpret_cast<const void *>(fused_kernel<8, 2>); break;
+            case 3: fn = reinterpret_cast<const void *>(fused_kernel<8, 3>); break;
+            case QV: fn = reinterpret_cast<const void *>(fused_kernel<8, QV>); break;
+            default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + 3>); break;
+        }
+    } else {
         fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
                     : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
                               : reinterpret_cast<const void *>(fused_kernel<N, 3>));
@@ -1091,8 +1162,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         g.step_tx = rem - g.step_ty * g.tiles_x;
     }
     {
-        const PlanK<N> &pk = plan.kparams<N>();
-        void *args[] = {const_cast<PlanK<N> *>(&pk), &tin, &tout, &g};
+        void *args[] = {const_cast<PlanK<N> *>(pk), &tin, &tout, &g};
         const cudaError_t le = cudaLaunchKernel(fn, dim3(unsigned(grid)), dim3(threads), args, L.total, st);
         if (le != cudaSuccess) {
             if (scratch) cudaFreeAsync(scratch, st);

@@ -31,6 +31,10 @@ struct PlanK {
     float sij[N][N];      // s_i * s_j (B = sij o C), rounded once from FP64
     float s[N];           // s_i
     uint32_t T2[N][N / 2]; // T[i][j] as a packed pair of IEEE halves (both lanes equal)
+    // JPEG-like quantiser of one call (N <= 8; filled per launch, zero in the plan):
+    static constexpr int QN = N <= 8 ? N : 1;
+    float qw[QN][QN];      // fl32(s_i s_j / Q_ij): Bbar = floor(fl32(C qw) + 1/2)
+    float qt[QN][QN];      // fl32(Q_ij / (s_i s_j)): the dequantised value in the C domain
 };
 
 // Host-side plan object behind the opaque rklt_plan handle.
@@ -82,6 +86,7 @@ struct FusedArgs {
     float *psnr;
     float *partials;   // caller-provided per-tile scratch, or null (library pool)
     int force_plain;   // 1: plain loads even when TMA would apply
+    const double *Q;   // N = 4, 8: JPEG-like quantiser (N*N, host); zcoef then holds int32 Bbar
 };
 
 rklt_status launch_fused_n4(const Plan &p, const FusedArgs &a, cudaStream_t st);
@@ -93,6 +98,7 @@ unsigned int take_status_n8();
 unsigned int take_status_n16();
 unsigned int take_status_n32();
 unsigned int take_status_split();
+unsigned int take_status_mssim();
 
 // host helpers (rklt_host.cpp)
 rklt_status fail(rklt_status st, const std::string &msg);

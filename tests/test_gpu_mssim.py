@@ -1,7 +1,7 @@
 """MSSIM (Sec. 4.1 quality measure) on the GPU against the FP64 oracle.
 
-Bound (from the FP32 arithmetic of the kernel): each second moment of the centred
-values is rounded along 22 steps, so a window's variance/covariance carries an error
+Bound (from the FP32 arithmetic of the kernel): each window sum of the centred
+second moments is rounded along 22 steps, so sigma_x^2 + sigma_y^2 and sigma_xy carry errors
 below 22 u (E[(x-128)^2] + E[(y-128)^2]), u = 2^-24, and its SSIM below four such
 terms over C2.  Averaged over the positions this is bounded by
 4 * 22 u * (mean (x-128)^2 + mean (y-128)^2) / C2 (the window weights sum to 1);
@@ -74,3 +74,21 @@ def test_mssim_identical_images_and_batches(rk, orc):
 def test_mssim_too_small_is_nan(rk):
     out = gpu_mssim(rk, np.zeros((10, 64), np.uint8), np.zeros((10, 64), np.uint8))
     assert np.isnan(out[0])
+
+
+def test_mssim_tma_and_plain_transport_agree(rk, orc):
+    """16-byte aligned rows (TMA chunk loads, several units in both directions, ragged
+    edges) against the oracle, and bit-identical to the plain-load transport."""
+    H, W = 1100, 608
+    x = si.ar1_image(H, W, 0.95, 95)
+    y = np.clip(x.astype(int) + si.ar1_image(H, W, 0.5, 96).astype(int) // 16 - 8, 0, 255).astype(np.uint8)
+    out = []
+    for transport in (0, 1):
+        rk.rklt_set_transport(transport)
+        try:
+            out.append(gpu_mssim(rk, x, y)[0])
+        finally:
+            rk.rklt_set_transport(0)
+    assert out[0] == out[1]
+    ref, _ = orc.mssim(x, y)
+    assert abs(out[0] - ref) <= bound(x, y), (out[0], ref)

@@ -105,3 +105,29 @@ def test_quant_rejects(rk):
         with pytest.raises(rk.RklTError) as e:
             rk.rklt_fused_quant(plan, d, 10, Q, s, ps)
         assert e.value.status == status
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_quant_tma_ragged_and_plain_transport(rk, orc, n):
+    """16-byte aligned rows (TMA tiles) with ragged edges in both directions, against the
+    oracle, and bit-identical to the plain-load transport of the same call."""
+    H, W = (200, 1040) if n == 8 else (196, 1040)
+    img = si.ar1_image(H, W, 0.9, 110 + n)
+    plan = rk.rklt_make(n, 0.95)
+    p = orc.Plan(n, 0.95)
+    Q = quantisers(n)["random"]
+    for r in (3, n * n // 2 + 1, n * n):
+        out = []
+        for transport in (0, 1):
+            rk.rklt_set_transport(transport)
+            try:
+                out.append(run(rk, plan, img, r, Q))
+            finally:
+                rk.rklt_set_transport(0)
+        sse_ref, qc_ref, rec_ref = orc.quant_pipeline(n, p.T, p.s, Q, img, r, want_coef=True, want_recon=True)
+        qc, rec, sse, _ = out[0]
+        assert np.array_equal(qc[0], qc_ref)
+        check_sse(sse[0], sse_ref, H, W, n)
+        check_recon_u8(rec[0], rec_ref, n)
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(a, b)
