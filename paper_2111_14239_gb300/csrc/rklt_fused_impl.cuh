@@ -498,7 +498,7 @@ __host__ __device__ constexpr int coop2_rounds() { return TH / N; }
 // Whether the coefficients are staged in shared memory (then written out
 // contiguously per block-row) rather than stored from the row pass directly.
 __host__ __device__ inline bool coop2_stage_coef(int N, int r) {
-    return int64_t(TH / N) * (TW / N) * (r | 1) * 4 <= (N == 8 ? 72 : 32) * 1024;
+    return int64_t(TH / N) * (TW / N) * (r | 1) * 4 <= 32 * 1024;
 }
 
 template <int N, int DRM, bool Q = false>
@@ -625,14 +625,22 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
     named_sync(1, NCONS);
 
     // ---- staged coefficients: each block-row's blocks are contiguous in the output
-    if (stage && g.zcoef) {
+    if (stage && g.zcoef && r > 0) {
         for (int round = 0; round < rows_in; round++) {
             float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * R + round) * bw +
                                     tc.tx * NB) * r;
             const float *src = Zs + round * NB * (r | 1);
+            // q = bq r + kq, advanced by NCONS = step_b r + step_k without a division
+            const int step_b = NCONS / r, step_k = NCONS - step_b * r;
+            int bq = ct / r, kq = ct - bq * r;
             for (int q = ct; q < nb_in * r; q += NCONS) {
-                const int bq = q / r;
-                dst[q] = src[bq * (r | 1) + (q - bq * r)];
+                dst[q] = src[bq * (r | 1) + kq];
+                bq += step_b;
+                kq += step_k;
+                if (kq >= r) {
+                    kq -= r;
+                    ++bq;
+                }
             }
         }
     }
@@ -701,15 +709,15 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
 namespace rklt {
 
 // Kernel variant V (picked on the host from the diagonal bound D):
-//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), else 3;
+//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), else 1;
 //   N = 32 with D <= 16, N = 16 with D <= 8: TC_V (tensor cores);
 //   N >= 16 otherwise: 1, 2, 3 = cooperative path (all block-rows at once) sized for
-//   Dr <= N/4, N/2, N;  N = 8: 2, 3 = the same path sized for Dr <= 4, 8;
-//   N = 4: 1 = cooperative path block-row by block-row.
+//   Dr <= N/4, N/2, N;  N = 8, real plans with D <= 4: 2 = the same path for Dr <= 4;
+//   N = 4, 8 otherwise: 1 = cooperative path block-row by block-row.
 // QV is added for the quantised form (N = 4, 8).
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
-    if (N == 8) return D <= REG_DMAX8 ? 0 : 3;
+    if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
     if (N == 32 && D <= TC_DMAX) return TC_V;
     if (N == 16 && D <= TC_DMAX16) return TC_V;
     const int Dr = D < N ? D : N;
@@ -720,7 +728,7 @@ __host__ __device__ inline int fused_variant(int N, int D) {
 // and tensor-core paths rely on T having entries in {0, +1, -1}.
 __host__ __device__ inline int real_variant(int N, int D) {
     if (N == 4) return 1;
-    if (N == 8) return D <= 4 ? 2 : 3;
+    if (N == 8) return D <= 4 ? 2 : 1;
     const int Dr = D < N ? D : N;
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
@@ -736,7 +744,6 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         constexpr int VB = vbase(V);
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
         else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
-        else if constexpr (N == 8 && VB == 3) return tile_coop2<8, 8, Q>(P, g, tile, tc, ct, Ys, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
         if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tc, ct, Ys, Zs);
@@ -1137,10 +1144,10 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     } else if constexpr (N == 8) {
         switch (V) {
             case 0: fn = reinterpret_cast<const void *>(fused_kernel<8, 0>); break;
+            case 1: fn = reinterpret_cast<const void *>(fused_kernel<8, 1>); break;
             case 2: fn = reinterpret_cast<const void *>(fused_kernel<8, 2>); break;
-            case 3: fn = reinterpret_cast<const void *>(fused_kernel<8, 3>); break;
             case QV: fn = reinterpret_cast<const void *>(fused_kernel<8, QV>); break;
-            default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + 3>); break;
+            default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + 1>); break;
         }
     } else {
         fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)

@@ -11,7 +11,7 @@
 //          16-byte aligned, TMA boxes of 256 + 16 columns (rows past the image read
 //          as 0) issued one chunk ahead, completion on an mbarrier; else plain loads;
 //   stage  the pixel pairs, centred at 128, as float4 (x, y, x^2 + y^2, x y) in
-//          shared memory (one conversion per pixel);
+//          shared memory (one conversion per pixel, four pixels per task);
 //   H      11-tap horizontal sums of the four quantities, four adjacent outputs
 //          per thread, each staged column read once and scattered into the four
 //          accumulators (packed FP32 FMAs: (x, y) and (x^2 + y^2, x y) pairs);
@@ -19,6 +19,8 @@
 //          (slot = output row mod 11, static because a chunk is 11 rows), adds the
 //          chunk's rows with the vertical weights, and finishes one output row per
 //          input row: SSIM from mu_x, mu_y, sigma_x^2 + sigma_y^2 and sigma_xy.
+// The float4 rows are XOR-swizzled within groups of 8 columns, so that lanes 1 or 4
+// columns apart hit distinct banks.
 // Only x^2 + y^2 is needed (the SSIM denominator uses sigma_x^2 + sigma_y^2), so four
 // window sums suffice.  Per thread, each chunk's SSIM values are summed in FP32 and
 // added to an FP64 total; per unit the totals are summed in a fixed order in FP64,
@@ -28,9 +30,9 @@
 // is a sum of 121 products rounded in FP32 (22 rounding steps along the two passes);
 // sigma_x^2 + sigma_y^2 = E[x^2 + y^2] - mu_x^2 - mu_y^2 then carries an absolute error
 // of about 22 u (E[(x-128)^2] + E[(y-128)^2]), u = 2^-24, sigma_xy half that, and SSIM
-// an error of at most four such terms over C2 (= 58.5).  The final quotient is the
-// IEEE one, and the products and differences are not contracted, so identical
-// images give SSIM = 1 exactly.
+// an error of at most four such terms over C2 (= 58.5).  The final quotient is taken
+// with the fast reciprocal (2 ulp), except that num = den gives 1; the products and
+// differences are not contracted, so identical images give SSIM = 1 exactly.
 #include <algorithm>
 #include <cmath>
 
@@ -41,16 +43,16 @@ namespace rklt {
 
 constexpr int MS_S = 11, MS_R = 5;
 constexpr int MS_WS = 256;                             // output columns per unit (one per thread)
-constexpr int MS_IC = MS_WS + MS_S - 1;                // 266 input columns
+constexpr int MS_IW = 268;                             // input columns staged (266 used), a multiple of 4
 constexpr int MS_CH = MS_S;                            // input rows per chunk
 constexpr int MS_NCH = 48;                             // chunks per unit
 constexpr int MS_SEG = MS_NCH * MS_CH - (MS_S - 1);    // 518 output rows per unit
 constexpr int MS_THREADS = 256;
 constexpr int MS_G = 4;                                // outputs per thread in the horizontal pass
-// float4 columns padded by one every 8 (conflict-free for lanes 8 columns apart)
-__host__ __device__ constexpr int ms_phys(int c) { return c + (c >> 3); }
-constexpr int MS_LDI = ms_phys(MS_IC - 1) + 1;         // 299 staged float4 per row
-constexpr int MS_LDH = ms_phys(MS_WS - 1) + 1;         // 287 horizontal-sum float4 per row
+// float4 column c of a row sits at c with its low 3 bits XOR (c / 4) mod 8
+__host__ __device__ constexpr int ms_phys(int c) { return (c & ~7) | ((c ^ (c >> 2)) & 7); }
+constexpr int MS_LDI = 272;                            // staged float4 per row
+constexpr int MS_LDH = MS_WS;                          // horizontal-sum float4 per row
 constexpr int MS_RAW = 3072;                           // one image's chunk: 11 x 256 bytes, then 11 x 16
 constexpr int MS_RAW_OFF = (MS_CH * MS_LDI + MS_CH * MS_LDH) * 16 + (MS_THREADS / 32) * 8;
 constexpr int MS_RAW_AL = (MS_RAW_OFF + 127) / 128 * 128;
@@ -118,26 +120,39 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
                 tma_load_3d(raw + MS_RAW + MS_CH * 256, &maps.y16, c0 + 256, y, img, bar);
             }
         };
-        // stage chunk m: input rows r0 + 11 m .. + 10, columns c0 .. c0 + 265
+        // stage chunk m: input rows r0 + 11 m .. + 10, columns c0 .. c0 + 267 (266 used),
+        // four columns per task
         const auto stage = [&](int m) {
-            for (int q = tid; q < MS_CH * MS_IC; q += MS_THREADS) {
-                const int rr = q / MS_IC, cc = q - rr * MS_IC;
-                float a = 0.0f, b = 0.0f;
+            for (int q = tid; q < MS_CH * (MS_IW / 4); q += MS_THREADS) {
+                const int rr = q / (MS_IW / 4), c4 = (q - rr * (MS_IW / 4)) * 4;
+                uint32_t wx = 0u, wy = 0u;
                 if (g.use_tma) {
-                    if (cc < 256 || box16) {
-                        const int o = cc < 256 ? rr * 256 + cc : MS_CH * 256 + rr * 16 + (cc - 256);
-                        a = float(raw[o]) - 128.0f;
-                        b = float(raw[MS_RAW + o]) - 128.0f;
+                    if (c4 < 256 || box16) {
+                        const int o = c4 < 256 ? rr * 256 + c4 : MS_CH * 256 + rr * 16 + (c4 - 256);
+                        wx = *reinterpret_cast<const uint32_t *>(raw + o);
+                        wy = *reinterpret_cast<const uint32_t *>(raw + MS_RAW + o);
                     }
                 } else {
-                    const int r = r0 + m * MS_CH + rr, c = c0 + cc;
-                    if (r < g.H && c < g.W) {
-                        a = float(xp[int64_t(r) * g.ldx + c]) - 128.0f;
-                        b = float(yp[int64_t(r) * g.ldy + c]) - 128.0f;
+                    const int r = r0 + m * MS_CH + rr;
+                    if (r < g.H) {
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int c = c0 + c4 + e;
+                            if (c < g.W) {
+                                wx |= uint32_t(xp[int64_t(r) * g.ldx + c]) << (8 * e);
+                                wy |= uint32_t(yp[int64_t(r) * g.ldy + c]) << (8 * e);
+                            }
+                        }
                     }
                 }
-                stg[rr * MS_LDI + ms_phys(cc)] =
-                    make_float4(a, b, __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(a, b));
+                float4 *dst = stg + rr * MS_LDI;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float a = float((wx >> (8 * e)) & 0xffu) - 128.0f;
+                    const float b = float((wy >> (8 * e)) & 0xffu) - 128.0f;
+                    dst[ms_phys(c4 + e)] =
+                        make_float4(a, b, __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(a, b));
+                }
             }
         };
         // wait for chunk m (TMA mode), stage it; false on a timeout (uniform over the CTA)
@@ -224,7 +239,7 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
                     const float num = __fmul_rn(__fadd_rn(__fmul_rn(2.0f * ux, uy), C1), __fadd_rn(2.0f * cxy, C2));
                     const float den = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), C1),
                                                 __fadd_rn(vsum, C2));
-                    csum += __fdiv_rn(num, den);
+                    csum += num == den ? 1.0f : __fdividef(num, den);
                 }
             }
             total += double(csum);
