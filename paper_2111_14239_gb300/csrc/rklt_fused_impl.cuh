@@ -57,7 +57,8 @@ constexpr int NCONS_TC = 256;    // consumer threads (8 warps) of the tensor-cor
 constexpr int NCONS_MAX = 256;
 constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchange buffer (floats)
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
-constexpr int REG_DMAX8 = 5;     // N = 8: register path up to this diagonal bound
+constexpr int REG_DMAX8 = 5;     // N = 8: two-CTA register path up to this diagonal bound
+constexpr int REG8_FULL = 5;     // variant number of the N = 8 register path for any D (one CTA per SM)
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
 constexpr int QV = 8;            // added to a variant number (N = 4, 8): quantised coefficients
 __host__ __device__ constexpr int vbase(int V) { return V & 7; }
@@ -102,6 +103,7 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
     constexpr int NP = N / 2;           // column pairs
     constexpr int DR = D < N ? D : N;   // rows / columns of C that carry retained terms
     constexpr int DA = DR > 0 ? DR : 1; // array extent (D = 0 keeps nothing)
+    constexpr bool FULL = D >= 2 * N - 1;  // every diagonal present: mask each entry by its zig-zag index
     const __half2 k1024 = __float2half2_rn(1024.0f);
     // pixels (A[k][2p], A[k][2p+1]) of column pair p as exact binary16 pairs
     auto px = [&](int k, int p) -> __half2 {
@@ -145,7 +147,7 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
                 float acc = 0.0f;
 #pragma unroll
                 for (int l = 0; l < H2; l++) acc = fmaf(P.T[j][l], (j & 1) ? d[l] : s[l], acc);
-                const bool keep = i + j < D - 1 || zz_index(N, i, j) < r;
+                const bool keep = FULL ? zz_index(N, i, j) < r : (i + j < D - 1 || zz_index(N, i, j) < r);
                 if constexpr (Q) {
                     const float bq = keep ? quant_code<N>(P, i, j, acc) : 0.0f;
                     Bq[i][j] = bq;
@@ -260,10 +262,12 @@ __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int 
     return block_core<N, D, Q>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
-template <int N, bool Q>
+template <int N, bool Q, bool ANYD>
 __device__ __forceinline__ float block_reg_dispatch(const PlanK<N> &P, uint8_t *blk, int D, int r, float *coef,
                                                     bool vec4, bool recon) {
-    if constexpr (N == 4) {
+    if constexpr (ANYD) {
+        return block_reg<N, 2 * N - 1, Q>(P, blk, r, coef, vec4, recon);
+    } else if constexpr (N == 4) {
         switch (D) {
             case 0: return block_reg<4, 0, Q>(P, blk, r, coef, vec4, recon);
             case 1: return block_reg<4, 1, Q>(P, blk, r, coef, vec4, recon);
@@ -324,7 +328,7 @@ struct TileWalker {
     }
 };
 
-template <int N, bool Q>
+template <int N, bool Q, bool ANYD = false>
 __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
@@ -337,7 +341,7 @@ __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g,
         if (gy * N >= g.H || gx * N >= g.W) continue;
         float *coef = nullptr;
         if (g.zcoef) coef = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(gy) * bw + gx) * g.r;
-        sse += block_reg_dispatch<N, Q>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
+        sse += block_reg_dispatch<N, Q, ANYD>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
                                      g.recon != nullptr);
     }
     return sse;
@@ -709,7 +713,8 @@ __device__ __forceinline__ float tile_coop2(const PlanK<N> &P, const FusedGeom &
 namespace rklt {
 
 // Kernel variant V (picked on the host from the diagonal bound D):
-//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), else 1;
+//   N = 4: 0 (register path, any D);  N = 8: 0 register path (D <= REG_DMAX8), else
+//   REG8_FULL (the register path for the full block, one CTA per SM);
 //   N = 32 with D <= 16, N = 16 with D <= 8: TC_V (tensor cores);
 //   N >= 16 otherwise: 1, 2, 3 = cooperative path (all block-rows at once) sized for
 //   Dr <= N/4, N/2, N;  N = 8, real plans with D <= 4: 2 = the same path for Dr <= 4;
@@ -717,7 +722,7 @@ namespace rklt {
 // QV is added for the quantised form (N = 4, 8).
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
-    if (N == 8) return D <= REG_DMAX8 ? 0 : 1;
+    if (N == 8) return D <= REG_DMAX8 ? 0 : REG8_FULL;
     if (N == 32 && D <= TC_DMAX) return TC_V;
     if (N == 16 && D <= TC_DMAX16) return TC_V;
     const int Dr = D < N ? D : N;
@@ -733,8 +738,9 @@ __host__ __device__ inline int real_variant(int N, int D) {
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
 
-// Consumer threads of kernel variant V.
+// Consumer threads of kernel variant V, and the CTAs per SM its registers are sized for.
 __host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : NCONS; }
+__host__ __device__ constexpr int kminb(int V) { return vbase(V) == REG8_FULL ? 1 : 2; }
 
 template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
@@ -743,6 +749,7 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         constexpr bool Q = V >= QV;
         constexpr int VB = vbase(V);
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
+        else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg<8, Q, true>(P, g, tile, tc, ct);
         else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
@@ -830,7 +837,7 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int 
     int ys = 0, zs = 0;
     if (V == TC_V) {
         zs = (NCONS_TC / 32) * TC_ZS * 4 + TC_TAB_BYTES;
-    } else if (N >= 16 || V >= 2) {  // all block-rows at once
+    } else if (N >= 16 || V == 2) {  // all block-rows at once
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
@@ -847,7 +854,7 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int 
 // The kernel: warps 0..7 consume; warp 8 produces in TMA mode (idle otherwise).
 // ---------------------------------------------------------------------------
 template <int N, int V>
-__global__ void __launch_bounds__(ncons(V) + 32, 2)
+__global__ void __launch_bounds__(ncons(V) + 32, kminb(V))
     fused_kernel(const __grid_constant__ PlanK<N> P, const __grid_constant__ CUtensorMap tm_in,
                  const __grid_constant__ CUtensorMap tm_out, const FusedGeom g) {
     constexpr int NC = ncons(V);
@@ -1132,7 +1139,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    g.stages = swz ? 6 : ((N >= 16 || vbase(V) >= 2) ? 3 : 4);
+    g.stages = swz ? 6 : ((N >= 16 || vbase(V) == 2) ? 3 : 4);
     const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, vbase(V));
     const void *fn = nullptr;
     if constexpr (N == 4) {
@@ -1146,8 +1153,9 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
             case 0: fn = reinterpret_cast<const void *>(fused_kernel<8, 0>); break;
             case 1: fn = reinterpret_cast<const void *>(fused_kernel<8, 1>); break;
             case 2: fn = reinterpret_cast<const void *>(fused_kernel<8, 2>); break;
+            case REG8_FULL: fn = reinterpret_cast<const void *>(fused_kernel<8, REG8_FULL>); break;
             case QV: fn = reinterpret_cast<const void *>(fused_kernel<8, QV>); break;
-            default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + 1>); break;
+            default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + REG8_FULL>); break;
         }
     } else {
         fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
