@@ -130,8 +130,9 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
         }
     }
     // row transform: C = Y T^T on the support i + j < D; zonal mask on the last diagonal
-    // (quantised: Bq = Bbar as exact FP32 integers, Cm = Bbar o Qtilde)
-    float Cm[DA][DA];
+    // (quantised: only Bq = Bbar is kept, as exact FP32 integers; the inverse forms
+    // Bbar o Qtilde where it reads it)
+    [[maybe_unused]] float Cm[Q ? 1 : DA][Q ? 1 : DA];
     [[maybe_unused]] float Bq[Q ? DA : 1][Q ? DA : 1];
 #pragma unroll
     for (int i = 0; i < DR; i++) {
@@ -151,7 +152,6 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
                 if constexpr (Q) {
                     const float bq = keep ? quant_code<N>(P, i, j, acc) : 0.0f;
                     Bq[i][j] = bq;
-                    Cm[i][j] = bq * P.qt[i][j];
                 } else {
                     Cm[i][j] = keep ? acc : 0.0f;
                 }
@@ -169,7 +169,7 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
                     for (int q = 0; q < 4; q++) {
                         const int k = 4 * k4 + q, i = zz_row(N, k), j = zz_col(N, k);
                         if constexpr (Q) v[q] = (i + j < D) ? __int_as_float(int(Bq[i < DA ? i : 0][j < DA ? j : 0])) : 0.0f;
-                        else v[q] = (i + j < D) ? P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0] : 0.0f;
+                        else v[q] = (i + j < D) ? P.sij[i][j] * Cm[Q ? 0 : (i < DA ? i : 0)][Q ? 0 : (j < DA ? j : 0)] : 0.0f;
                     }
                     *reinterpret_cast<float4 *>(coef + 4 * k4) = make_float4(v[0], v[1], v[2], v[3]);
                 }
@@ -180,7 +180,7 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
                 const int i = zz_row(N, k), j = zz_col(N, k);
                 if (i + j < D && k < r) {
                     if constexpr (Q) coef[k] = __int_as_float(int(Bq[i < DA ? i : 0][j < DA ? j : 0]));
-                    else coef[k] = P.sij[i][j] * Cm[i < DA ? i : 0][j < DA ? j : 0];
+                    else coef[k] = P.sij[i][j] * Cm[Q ? 0 : (i < DA ? i : 0)][Q ? 0 : (j < DA ? j : 0)];
                 }
             }
         }
@@ -195,8 +195,11 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 #pragma unroll
             for (int j = 0; j < DR; j++) {
                 if (i + j < D) {
-                    if (j & 1) o = fmaf(Cm[i][j], P.Ti[l][j], o);
-                    else e = fmaf(Cm[i][j], P.Ti[l][j], e);
+                    float cm;
+                    if constexpr (Q) cm = Bq[i][j] * P.qt[i][j];
+                    else cm = Cm[i][j];
+                    if (j & 1) o = fmaf(cm, P.Ti[l][j], o);
+                    else e = fmaf(cm, P.Ti[l][j], e);
                 }
             }
             X[i][l] = e + o;
@@ -262,12 +265,10 @@ __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int 
     return block_core<N, D, Q>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
-template <int N, bool Q, bool ANYD>
+template <int N, bool Q>
 __device__ __forceinline__ float block_reg_dispatch(const PlanK<N> &P, uint8_t *blk, int D, int r, float *coef,
                                                     bool vec4, bool recon) {
-    if constexpr (ANYD) {
-        return block_reg<N, 2 * N - 1, Q>(P, blk, r, coef, vec4, recon);
-    } else if constexpr (N == 4) {
+    if constexpr (N == 4) {
         switch (D) {
             case 0: return block_reg<4, 0, Q>(P, blk, r, coef, vec4, recon);
             case 1: return block_reg<4, 1, Q>(P, blk, r, coef, vec4, recon);
@@ -328,7 +329,62 @@ struct TileWalker {
     }
 };
 
-template <int N, bool Q, bool ANYD = false>
+// N = 8 with any D (one CTA per SM): one block per consumer thread, warp w owning
+// block-row w of the tile (32 blocks, one per lane).  Coefficients are staged per
+// warp in shared memory (block stride STG8_LD floats: 16-byte aligned, and lanes 272
+// bytes apart hit distinct banks) and leave as one contiguous run per block-row.
+constexpr int STG8_LD = 68;
+template <bool Q>
+__device__ __forceinline__ float tile_reg8_full(const PlanK<8> &P, const FusedGeom &g, uint8_t *tile,
+                                                const TileCoord &tc, int ct, float *Zs) {
+    constexpr int BPR = TW / 8;
+    static_assert((TH / 8) * BPR == NCONS, "one block per consumer thread");
+    const int lane = ct & 31, w = ct >> 5;
+    const int bw = g.W / 8, r = g.r;
+    const int gy = tc.ty * (TH / 8) + w, gx = tc.tx * BPR + lane;
+    const bool row_in = gy * 8 < g.H;
+    const bool coef = g.zcoef != nullptr && r > 0;
+    float *stage = coef ? Zs + (w * 32 + lane) * STG8_LD : nullptr;
+    float sse = 0.0f;
+    if (row_in && gx * 8 < g.W)
+        sse = block_reg<8, 15, Q>(P, tile + w * 8 * TW + lane * 8, r, stage, (r & 3) == 0, g.recon != nullptr);
+    if (coef && row_in) {
+        __syncwarp();
+        const int nb = min(BPR, bw - tc.tx * BPR);  // blocks of this block-row inside the image
+        float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(gy) * bw + tc.tx * BPR) * r;
+        const float *src = Zs + w * 32 * STG8_LD;
+        // element c = b n + k of the run (n per block), advanced by 32 without a division
+        if (g.coef_vec4) {
+            const int n = r >> 2, sb = 32 / n, sk = 32 - sb * n;
+            int b = lane / n, k = lane - b * n;
+            for (int c = lane; c < nb * n; c += 32) {
+                reinterpret_cast<float4 *>(dst)[c] = *reinterpret_cast<const float4 *>(src + b * STG8_LD + 4 * k);
+                b += sb;
+                k += sk;
+                if (k >= n) {
+                    k -= n;
+                    ++b;
+                }
+            }
+        } else {
+            const int sb = 32 / r, sk = 32 - sb * r;
+            int b = lane / r, k = lane - b * r;
+            for (int c = lane; c < nb * r; c += 32) {
+                dst[c] = src[b * STG8_LD + k];
+                b += sb;
+                k += sk;
+                if (k >= r) {
+                    k -= r;
+                    ++b;
+                }
+            }
+        }
+        __syncwarp();  // the staging area is rewritten by the next tile
+    }
+    return sse;
+}
+
+template <int N, bool Q>
 __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
@@ -341,7 +397,7 @@ __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g,
         if (gy * N >= g.H || gx * N >= g.W) continue;
         float *coef = nullptr;
         if (g.zcoef) coef = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(gy) * bw + gx) * g.r;
-        sse += block_reg_dispatch<N, Q, ANYD>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
+        sse += block_reg_dispatch<N, Q>(P, tile + by * N * TW + bx * N, g.D, g.r, coef, g.coef_vec4 != 0,
                                      g.recon != nullptr);
     }
     return sse;
@@ -749,7 +805,7 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         constexpr bool Q = V >= QV;
         constexpr int VB = vbase(V);
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
-        else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg<8, Q, true>(P, g, tile, tc, ct);
+        else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg8_full<Q>(P, g, tile, tc, ct, Zs);
         else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
@@ -841,6 +897,8 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int 
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
+    } else if (N == 8 && V == REG8_FULL) {  // per-warp coefficient staging
+        zs = NCONS * STG8_LD * 4;
     } else if (V == 1) {  // N = 4, 8 cooperative path, block-row by block-row
         ys = N * LDY * 4;
         zs = (TW / N) * r * 4;
