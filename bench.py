@@ -40,10 +40,10 @@ KERNEL = {4: "fused_kernel<4, 0>", 8: "fused_kernel<8, 0>", 16: "fused_kernel<16
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
     # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
-    "fused_kernel<4, 0>": 268507136 + 343941632,
-    "fused_kernel<8, 0>": 268545024 + 347807488,
-    "fused_kernel<16, 4>": 268521984 + 338144256,
-    "fused_kernel<32, 4>": 268619520 + 342074112,
+    "fused_kernel<4, 0>": 268505600 + 343873792,
+    "fused_kernel<8, 0>": 268540928 + 347969792,
+    "fused_kernel<16, 4>": 268554752 + 338125312,
+    "fused_kernel<32, 4>": 268501760 + 343054848,
 }
 
 
@@ -316,6 +316,8 @@ def run_ours(args):
                          ("r_sweep_256x512", lambda: leg_sweep(rk, dev, stream)),
                          ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream)),
                          ("serving", lambda: leg_serve(rk, dev, args.serve_seconds))):
+            if args.legs and name not in args.legs.split(","):
+                continue
             try:
                 workloads[name] = fn()
             except Exception as e:  # report, do not lose the main line
@@ -558,6 +560,7 @@ def main():
     ap.add_argument("--block-sizes", default="4,8,16,32", help="subset of N (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the single/sweep/batch/serving legs")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--legs", default="", help="comma-separated subset of the extra legs (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
