@@ -1,0 +1,199 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configurations the
+benchmark times, against the FP64 oracle on sampled outputs it computes one block or
+one image at a time, plus properties that hold at any size.
+
+  16 x 4096^2, N in {4, 8, 16, 32}, r = N^2/8 (one batched fused launch per N):
+      sampled blocks -> integer stage recovered bit-exact from the coefficients,
+      coefficients, 8-bit reconstruction; every image's SSE / PSNR;
+  one 512^2 image, N = 8, r = 10: the whole output;
+  r-sweep of 256 x 512^2 over the ten grid plans: sampled (image, plan, r);
+  2000 uneven crops in one autotuned graph batch: sampled images;
+  quantisation (N = 8, r = 64) on the 16 x 4096^2 batch: sampled blocks bit-exact;
+  MSSIM of a 4096^2 pair: against the oracle, and alone = inside the batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth_inputs as si
+from test_gpu_parity import check_coef, check_recon_u8, check_sse
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rk():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2111_14239_gb300 as rk
+    rk.rklt_set_transport(0)
+    return rk
+
+
+@pytest.fixture(scope="module")
+def roofline():
+    imgs = si.roofline_batch()          # 16 x 4096 x 4096, rho 0.95, seeds 2000..
+    return imgs, torch.from_numpy(imgs).cuda()
+
+
+def sample_blocks(nimg, bh, bw, seed, k=60):
+    g = np.random.default_rng(seed)
+    fixed = [(0, 0, 0), (nimg - 1, bh - 1, bw - 1), (0, bh - 1, 0), (nimg - 1, 0, bw - 1)]
+    return fixed + [(int(g.integers(nimg)), int(g.integers(bh)), int(g.integers(bw))) for _ in range(k)]
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
+def test_roofline_workload(rk, orc, roofline, n):
+    imgs, d = roofline
+    nimg, H, W = imgs.shape
+    r = n * n // 8
+    plan = rk.rklt_make(n, 0.95)
+    p = orc.Plan(n, 0.95)
+    bh, bw = H // n, W // n
+    zc = torch.empty(nimg * bh * bw * r, device="cuda")
+    rec = torch.empty_like(d)
+    sse = torch.empty(nimg, dtype=torch.float64, device="cuda")
+    ps = torch.empty(nimg, device="cuda")
+    rk.rklt_fused_batched(plan, d, r, sse, ps, zcoef=zc, recon=rec)
+    torch.cuda.synchronize()
+    rk.rklt_device_status()
+    zcv = zc.view(nimg, bh, bw, r)
+    zr, zcol = orc.zigzag(n)
+    sij = np.float32(np.outer(p.s, p.s))[zr[:r], zcol[:r]].astype(np.float64)
+    for (i, by, bx) in sample_blocks(nimg, bh, bw, 100 + n):
+        blk = np.ascontiguousarray(imgs[i, by * n:(by + 1) * n, bx * n:(bx + 1) * n])
+        _, zref, rref = orc.pipeline(n, p.That, blk, r, want_coef=True, want_recon=True)
+        got = zcv[i, by, bx].cpu().numpy().astype(np.float64)
+        check_coef(got[None], zref)
+        # b = fl32(fl32(s_i s_j) C) with C an exact integer below 2^23: C comes back exactly
+        C = orc.int_stage(n, p.T, blk)[0][zr[:r], zcol[:r]]
+        assert np.array_equal(np.rint(got / sij).astype(np.int64), C)
+        check_recon_u8(rec[i, by * n:(by + 1) * n, bx * n:(bx + 1) * n].cpu().numpy(), rref, n)
+    sse_h, ps_h = sse.cpu().numpy(), ps.cpu().numpy()
+    for i in range(nimg):
+        ref, _, _ = orc.pipeline(n, p.That, imgs[i], r)
+        check_sse(sse_h[i], ref, H, W, n)
+        assert abs(ps_h[i] - 10 * math.log10(255 ** 2 * H * W / ref)) <= 1e-3
+
+
+def test_single_512_whole_output(rk, orc):
+    img = si.single_512()
+    n, r = 8, 10
+    plan = rk.rklt_make(n, 0.95)
+    p = orc.Plan(n, 0.95)
+    d = torch.from_numpy(img).cuda()
+    zc = torch.empty((512 // n) ** 2 * r, device="cuda")
+    rec = torch.empty_like(d)
+    sse = torch.empty(1, dtype=torch.float64, device="cuda")
+    ps = torch.empty(1, device="cuda")
+    rk.rklt_fused(plan, d, r, sse, ps, zcoef=zc, recon=rec)
+    torch.cuda.synchronize()
+    ref, zref, rref = orc.pipeline(n, p.That, img, r, want_coef=True, want_recon=True)
+    check_coef(zc.view(-1, r).cpu().numpy(), zref)
+    check_recon_u8(rec.cpu().numpy(), rref, n)
+    check_sse(float(sse.item()), ref, 512, 512, n)
+    assert abs(float(ps.item()) - 10 * math.log10(255 ** 2 * 512 * 512 / ref)) <= 1e-3
+
+
+def test_rsweep_workload_sampled(rk, orc):
+    imgs, _ = si.sweep_batch()          # 256 x 512 x 512
+    plans = [rk.rklt_make(8, rho) for rho in si.GRID_RHOS]
+    d = torch.from_numpy(imgs).cuda()
+    sse = torch.empty((256, len(plans), 64), dtype=torch.float64, device="cuda")
+    ps = torch.empty((256, len(plans), 64), device="cuda")
+    rk.rklt_rsweep(plans, d, sse, ps)
+    torch.cuda.synchronize()
+    rk.rklt_device_status()
+    sse, ps = sse.cpu().numpy(), ps.cpu().numpy()
+    for i in (0, 97, 255):
+        for k, rho in enumerate(si.GRID_RHOS):
+            p = orc.Plan(8, rho)
+            for r in (1, 10, 37, 63):
+                ref, _, _ = orc.pipeline(8, p.That, imgs[i], r)
+                check_sse(sse[i, k, r - 1], ref, 512, 512, 8)
+                assert abs(ps[i, k, r - 1] - 10 * math.log10(255 ** 2 * 512 * 512 / ref)) <= 1e-3
+            assert sse[i, k, 63] == 0.0 and ps[i, k, 63] == math.inf
+
+
+def test_batch_workload_sampled(rk, orc):
+    items = si.mixed_items(2000)
+    bases = si.base_fields(sorted({si.nearest_grid_rho(it.rho) for it in items}), 4096, 6000)
+    hosts = si.mixed_batch(items, bases)
+    plans = [rk.rklt_make(8, rho) for rho in si.GRID_RHOS]
+    pidx = {rho: k for k, rho in enumerate(si.GRID_RHOS)}
+    bufs, entries = [], []
+    for it, h in zip(items, hosts):
+        dd = torch.from_numpy(np.ascontiguousarray(h)).cuda()
+        rec = torch.empty_like(dd)
+        zc = torch.empty((it.h // 8) * (it.w // 8) * it.r, device="cuda")
+        bufs.append((dd, rec, zc))
+        entries.append((dd, pidx[si.nearest_grid_rho(it.rho)], it.r, zc, rec))
+    sse = torch.empty(2000, dtype=torch.float64, device="cuda")
+    ps = torch.empty(2000, device="cuda")
+    batch = rk.rklt_batch_create(rk.make_items(entries), plans, sse, ps, autotune=True)
+    try:
+        batch.run(None)
+        torch.cuda.synchronize()
+    finally:
+        batch.close()
+    rk.rklt_device_status()
+    sse_h = sse.cpu().numpy()
+    px = np.array([it.h * it.w for it in items])
+    picks = [int(np.argmin(px)), int(np.argmax(px)), 0, 1999] + list(np.random.default_rng(7).integers(0, 2000, 6))
+    for k in picks:
+        it, h = items[k], hosts[k]
+        p = orc.Plan(8, si.nearest_grid_rho(it.rho))
+        ref, zref, rref = orc.pipeline(8, p.That, h, it.r, want_coef=True, want_recon=True)
+        check_sse(sse_h[k], ref, it.h, it.w, 8)
+        check_coef(bufs[k][2].view(-1, it.r).cpu().numpy(), zref)
+        check_recon_u8(bufs[k][1].cpu().numpy(), rref, 8)
+
+
+def test_quant_workload_sampled(rk, orc, roofline):
+    imgs, d = roofline
+    nimg, H, W = imgs.shape
+    n, r = 8, 64
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    Q = 2.0 + 3.0 * (i + j)
+    plan = rk.rklt_make(n, 0.95)
+    p = orc.Plan(n, 0.95)
+    bh, bw = H // n, W // n
+    qc = torch.empty(nimg * bh * bw * r, dtype=torch.int32, device="cuda")
+    rec = torch.empty_like(d)
+    sse = torch.empty(nimg, dtype=torch.float64, device="cuda")
+    ps = torch.empty(nimg, device="cuda")
+    rk.rklt_fused_quant(plan, d, r, Q, sse, ps, qcoef=qc, recon=rec)
+    torch.cuda.synchronize()
+    rk.rklt_device_status()
+    qcv = qc.view(nimg, bh, bw, r)
+    for (im, by, bx) in sample_blocks(nimg, bh, bw, 300):
+        blk = np.ascontiguousarray(imgs[im, by * n:(by + 1) * n, bx * n:(bx + 1) * n])
+        _, qref, rref = orc.quant_pipeline(n, p.T, p.s, Q, blk, r, want_coef=True, want_recon=True)
+        assert np.array_equal(qcv[im, by, bx].cpu().numpy(), qref[0])
+        check_recon_u8(rec[im, by * n:(by + 1) * n, bx * n:(bx + 1) * n].cpu().numpy(), rref, n)
+    for im in (0, nimg - 1):
+        ref, _, _ = orc.quant_pipeline(n, p.T, p.s, Q, imgs[im], r)
+        check_sse(float(sse[im].item()), ref, H, W, n)
+
+
+def test_mssim_workload(rk, orc, roofline):
+    imgs, d = roofline
+    n, r = 8, 8
+    plan = rk.rklt_make(n, 0.95)
+    rec = torch.empty_like(d)
+    s = torch.empty(d.shape[0], dtype=torch.float64, device="cuda")
+    p = torch.empty(d.shape[0], device="cuda")
+    rk.rklt_fused_batched(plan, d, r, s, p, recon=rec)
+    out = torch.empty(d.shape[0], dtype=torch.float64, device="cuda")
+    rk.rklt_mssim(d, rec, out)
+    one = torch.empty(1, dtype=torch.float64, device="cuda")
+    rk.rklt_mssim(d[0], rec[0], one)
+    torch.cuda.synchronize()
+    assert float(one.item()) == float(out[0].item())
+    x, y = imgs[0], rec[0].cpu().numpy()
+    ref, _ = orc.mssim(x, y)
+    m = np.mean((x.astype(np.float64) - 128) ** 2) + np.mean((y.astype(np.float64) - 128) ** 2)
+    bound = 4 * 22 * 2.0 ** -24 * m / (0.03 * 255) ** 2 + 1e-6
+    assert abs(float(out[0].item()) - ref) <= bound
