@@ -134,8 +134,8 @@ struct TcLane {
 // halves are equal appears twice), so they load straight into place:
 //   k = 0, 1  I1 B of y' n-tile k: hi, hi (even i), hi, hi (odd i) of 2^6 T^{-1}[y'][i]
 //   k = 2, 3  I2 B of x' n-tile k - 2: the same for T^{-1}[x'][j]
-//   k = 4, 5  staging slots of accumulator elements q = 4 (k - 4) .. + 3: the zig-zag
-//             position when retained, else the spare slot TC_ZS - 1
+//   k = 4, 5  staging byte offsets of accumulator elements q = 4 (k - 4) .. + 3: 4 x the
+//             zig-zag position when retained, else 4 x the spare slot TC_ZS - 1
 //   k = 6, 7  2^12 s_i s_j of those elements
 //   k = 8, 9  1.0 when retained, else 0.0
 //   k = 10, 11  F1 A fragments of k-step k - 10: T[j][x], rows j = 2g (even), 2g + 1 (odd)
@@ -204,7 +204,7 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
         const int nt = q >> 2, e = q & 3;
         const int j = 2 * g + (e >> 1), i = 4 * t + 2 * (e & 1) + nt;
         const int z = zz_index(32, i, j);
-        zp[q] = uint32_t(z < r ? z : TC_ZS - 1);
+        zp[q] = uint32_t(4 * (z < r ? z : TC_ZS - 1));
         bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
         kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
     }
@@ -221,8 +221,11 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
 // staging buffer (shared-window address).  Returns the lane's share of the block's
 // SSE; writes the 8-bit reconstruction in place when `recon`, and the r normalised
 // coefficients to zg (if not null).
+template <bool FAST>
 __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, int r,
-                                            float *zg, uint32_t zs, bool recon, bool vec4) {
+                                            float *zg, uint32_t zs, bool recon_, bool vec4_) {
+    // FAST: coefficients (16-byte aligned, r % 4 == 0) and reconstruction both wanted
+    const bool recon = FAST || recon_, vec4 = FAST || vec4_;
     // the lane's rows: q = 0: g, 1: 8 + g, 2: 31 - g, 3: 23 - g
     // rows q = 0, 1 are [off[0][.]] and [off[0][.] + 1024], rows 2, 3 [off[1][.]] and
     // [off[1][.] - 1024]
@@ -280,12 +283,12 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     uint32_t ch[2][2], cl[2][2];
 #pragma unroll
     for (int nt = 0; nt < 2; nt++) {
-        if (zg) {
+        if (FAST || zg) {
             const uint4 zp = lds128(tabl + (4 + nt) * 512), bs = lds128(tabl + (6 + nt) * 512);
-            sts_f32(zs + 4 * zp.x, __uint_as_float(bs.x) * d2[nt][0]);
-            sts_f32(zs + 4 * zp.y, __uint_as_float(bs.y) * d2[nt][1]);
-            sts_f32(zs + 4 * zp.z, __uint_as_float(bs.z) * d2[nt][2]);
-            sts_f32(zs + 4 * zp.w, __uint_as_float(bs.w) * d2[nt][3]);
+            sts_f32(zs + zp.x, __uint_as_float(bs.x) * d2[nt][0]);
+            sts_f32(zs + zp.y, __uint_as_float(bs.y) * d2[nt][1]);
+            sts_f32(zs + zp.z, __uint_as_float(bs.z) * d2[nt][2]);
+            sts_f32(zs + zp.w, __uint_as_float(bs.w) * d2[nt][3]);
         }
         const uint4 kp = lds128(tabl + (8 + nt) * 512);
         const float2 v0 = __fmul2_rn(make_float2(d2[nt][0], d2[nt][1]),
@@ -367,9 +370,12 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
         }
     }
     // ---- coefficients of the block, contiguous in the output
-    if (zg) {
+    if (FAST || zg) {
         __syncwarp();
-        if (vec4) {
+        if (FAST) {  // r <= 136 (D <= 16): at most two float4 per lane
+            if (4 * lane < r) *reinterpret_cast<uint4 *>(zg + 4 * lane) = lds128(zs + 16 * lane);
+            if (4 * lane + 128 < r) *reinterpret_cast<uint4 *>(zg + 4 * lane + 128) = lds128(zs + 16 * lane + 512);
+        } else if (vec4) {
             for (int k = 4 * lane; k < r; k += 128) {
                 const uint4 v = lds128(zs + 4 * k);
                 *reinterpret_cast<uint4 *>(zg + k) = v;
@@ -383,6 +389,7 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
 }
 
 // The 16 blocks of one tile: warp w takes block column w of both block rows.
+template <bool FAST>
 __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                          const TileCoord &tc, int ct, uint32_t zs) {
     const int bx = ct >> 5, lane = ct & 31;
@@ -392,11 +399,11 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
     float sse = 0.0f;
     if (bx >= nb_in) return sse;
     for (int by = 0; by < rows_in; by++) {
-        float *zg = g.zcoef ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
-                                         int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + bx) * g.r
-                            : nullptr;
-        sse += tc_block32(c, tabl, smem_u32(tile) + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
-                          g.coef_vec4 != 0);
+        float *zg = (FAST || g.zcoef) ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
+                                                   int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + bx) * g.r
+                                      : nullptr;
+        sse += tc_block32<FAST>(c, tabl, smem_u32(tile) + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
+                                g.coef_vec4 != 0);
     }
     return sse;
 }
@@ -424,7 +431,7 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
 //   k = 6     I1 lo digits: class 0 vb3 0, 1, class 1 vb3 0, 1
 //   k = 7     I2 B: (hi, hi) of 2^6 T^{-1}[x][2t, 2t+1] for n-tile 0, then n-tile 1
 //   k = 8     I2 lo digits for n-tile 0, 1
-//   k = 9, 10   staging slots (2 vb + hb) r + z of accumulator elements q = 4 class + e
+//   k = 9, 10   staging byte offsets 4 ((2 vb + hb) r + z) of accumulator elements q = 4 class + e
 //   k = 11, 12  2^12 s_i s_j;  k = 13, 14  1.0 when retained, else 0.0
 constexpr int TC16_TAB = 15;
 // ---------------------------------------------------------------------------
@@ -493,7 +500,7 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
         const int vb = t >> 1, hb = e >> 1;
         const int i = 2 * ((2 * t + (e & 1)) & 3) + cls, j = g;
         const int z = zz_index(16, i, j);
-        zp[q] = uint32_t(z < r ? (2 * vb + hb) * r + z : TC_ZS - 1);
+        zp[q] = uint32_t(4 * (z < r ? (2 * vb + hb) * r + z : TC_ZS - 1));
         bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
         kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
     }
@@ -508,9 +515,10 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
 // One 32 x 32 region (four 16 x 16 blocks) by one warp.  `in` has bit 2 vb + hb set
 // for the blocks inside the image (all four in the interior); only those add to the
 // SSE.  The staging buffer receives each block's r coefficients at (2 vb + hb) r.
-template <bool ALL_IN>
+template <bool ALL_IN, bool FAST>
 __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, uint32_t zs,
-                                             bool coef, bool recon, int in) {
+                                             bool coef_, bool recon_, int in) {
+    const bool coef = FAST || coef_, recon = FAST || recon_;
     const int t = lane & 3;
     // word w (x block) of row q: q = 0 [off[0][w]], 1 [+2048], 2 [off[1][w]], 3 [+2048]
     const auto ld_word = [&](int q, int w) -> uint32_t {
@@ -566,10 +574,10 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     for (int cls = 0; cls < 2; cls++) {
         if (coef) {
             const uint4 zp = lds128(tabl + (9 + cls) * 512), bs = lds128(tabl + (11 + cls) * 512);
-            sts_f32(zs + 4 * zp.x, __uint_as_float(bs.x) * d2[cls][0]);
-            sts_f32(zs + 4 * zp.y, __uint_as_float(bs.y) * d2[cls][1]);
-            sts_f32(zs + 4 * zp.z, __uint_as_float(bs.z) * d2[cls][2]);
-            sts_f32(zs + 4 * zp.w, __uint_as_float(bs.w) * d2[cls][3]);
+            sts_f32(zs + zp.x, __uint_as_float(bs.x) * d2[cls][0]);
+            sts_f32(zs + zp.y, __uint_as_float(bs.y) * d2[cls][1]);
+            sts_f32(zs + zp.z, __uint_as_float(bs.z) * d2[cls][2]);
+            sts_f32(zs + zp.w, __uint_as_float(bs.w) * d2[cls][3]);
         }
         const uint4 kp = lds128(tabl + (13 + cls) * 512);
         const float2 v0 = __fmul2_rn(make_float2(d2[cls][0], d2[cls][1]),
@@ -647,6 +655,7 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
 }
 
 // The 16 regions of one tile (N = 16): warp w takes region column w of both region rows.
+template <bool FAST>
 __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                            const TileCoord &tc, int ct, uint32_t zs) {
     const int lane = ct & 31, w = ct >> 5;
@@ -657,28 +666,29 @@ __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const
     const int r = g.r;
     float sse = 0.0f;
     if (2 * w >= nb_in) return sse;
+    const bool coef = FAST || g.zcoef != nullptr;
+    const bool cols2 = 2 * w + 1 < nb_in;   // both block columns of the warp inside
     for (int ry = 0; ry < 2; ry++) {
         if (2 * ry >= rows_in) break;
-        int in = 0;
-#pragma unroll
-        for (int vb = 0; vb < 2; vb++)
-#pragma unroll
-            for (int hb = 0; hb < 2; hb++)
-                if (2 * ry + vb < rows_in && 2 * w + hb < nb_in) in |= 1 << (2 * vb + hb);
+        const bool rows2 = 2 * ry + 1 < rows_in;
+        const int in = (rows2 && cols2) ? 15 : (1 | (cols2 ? 2 : 0) | (rows2 ? 4 | (cols2 ? 8 : 0) : 0));
         const uint32_t blk = t32 + ry * 32 * 128;
-        const bool coef = g.zcoef != nullptr;
-        if (in == 15) sse += tc16_region<true>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
-        else sse += tc16_region<false>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        if (in == 15) sse += tc16_region<true, FAST>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        else sse += tc16_region<false, FAST>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
         if (coef) {
+            // coefficients of the region's first block
+            float *zrow0 = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * (TH / 16) + 2 * ry) * bw +
+                                      tc.tx * (TW / 16) + 2 * w) * r;
             __syncwarp();
 #pragma unroll
             for (int vb = 0; vb < 2; vb++) {
                 if (!((in >> (2 * vb)) & 1)) continue;
                 const int n = ((in >> (2 * vb + 1)) & 1) ? 2 * r : r;   // floats of this block row
-                float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
-                                        int64_t(tc.ty * (TH / 16) + 2 * ry + vb) * bw + tc.tx * (TW / 16) + 2 * w) * r;
+                float *dst = zrow0 + (vb ? int64_t(bw) * r : int64_t(0));
                 const uint32_t src = zs + 4 * (2 * vb * r);
-                if (g.coef_vec4) {
+                if (FAST) {  // n <= 72 (D <= 8): one float4 per lane at most
+                    if (4 * lane < n) *reinterpret_cast<uint4 *>(dst + 4 * lane) = lds128(src + 16 * lane);
+                } else if (g.coef_vec4) {
                     for (int k = 4 * lane; k < n; k += 128) *reinterpret_cast<uint4 *>(dst + k) = lds128(src + 4 * k);
                 } else {
                     for (int k = lane; k < n; k += 32) dst[k] = __uint_as_float(lds32(src + 4 * k));
