@@ -917,7 +917,9 @@ __global__ void __launch_bounds__(ncons(V) + 32, kminb(V))
                  const __grid_constant__ CUtensorMap tm_out, const FusedGeom g) {
     constexpr int NC = ncons(V);
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1 KB aligned, by an offset from the shared array (so that every pointer derived
+    // from it stays a shared-space pointer: LDS / STS with immediate offsets)
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int NST = g.stages;  // ring depth (<= STAGES)
     const SmemLayout L = smem_layout<N>(g.use_tma ? NST : 1, g.r, g.D, vbase(V));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar_off);
