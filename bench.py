@@ -40,10 +40,10 @@ KERNEL = {4: "fused_kernel<4, 0>", 8: "fused_kernel<8, 0>", 16: "fused_kernel<16
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
     # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
-    "fused_kernel<4, 0>": 268505600 + 343873792,
-    "fused_kernel<8, 0>": 268540928 + 347969792,
-    "fused_kernel<16, 4>": 268554752 + 338125312,
-    "fused_kernel<32, 4>": 268501760 + 343054848,
+    "fused_kernel<4, 0>": 268508160 + 343627264,
+    "fused_kernel<8, 0>": 268548096 + 346659328,
+    "fused_kernel<16, 4>": 268536576 + 339311872,
+    "fused_kernel<32, 4>": 268518144 + 342444544,
 }
 
 
