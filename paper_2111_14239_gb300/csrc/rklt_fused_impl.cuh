@@ -371,7 +371,9 @@ __device__ __forceinline__ float tile_reg_d(const PlanK<N> &P, const FusedGeom &
     const int bw = g.W / N, r = g.r;
     const bool full = (tc.ty + 1) * TH <= g.H && (tc.tx + 1) * TW <= g.W;
     float *zimg = (FAST || g.zcoef) ? g.zcoef + int64_t(tc.img) * g.blocks_per_img * r : nullptr;
-    const bool vec4 = g.coef_vec4 != 0, recon = g.recon != nullptr;
+    // the 8-bit result is always written into the shared tile: a tile is stored back
+    // only when a reconstruction is wanted, so the write needs no branch
+    const bool vec4 = g.coef_vec4 != 0, recon = true;
     float sse = 0.0f;
 #pragma unroll 1
     for (int q = ct; q < BPT; q += NCONS) {

@@ -148,10 +148,12 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
                 float4 *dst = stg + rr * MS_LDI;
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const float a = float((wx >> (8 * e)) & 0xffu) - 128.0f;
-                    const float b = float((wy >> (8 * e)) & 0xffu) - 128.0f;
-                    dst[ms_phys(c4 + e)] =
-                        make_float4(a, b, __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(a, b));
+                    // byte e under the exponent of 2^23 is the float 2^23 + byte (exact)
+                    const uint32_t sel = 0x7440u | uint32_t(e);
+                    const float a = __uint_as_float(__byte_perm(wx, 0x4B000000u, sel)) - 8388736.0f;
+                    const float b = __uint_as_float(__byte_perm(wy, 0x4B000000u, sel)) - 8388736.0f;
+                    // products and sum of integers below 2^15: exact in any order
+                    dst[ms_phys(c4 + e)] = make_float4(a, b, fmaf(a, a, b * b), a * b);
                 }
             }
         };
@@ -231,7 +233,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
                 // output row o = j - 10 is complete (slot (qq + 1) mod 11)
                 const int o = m * MS_CH + qq - (MS_S - 1);
                 const int slot = (qq + 1) % MS_S;
-                if (o >= 0 && o < orows && col_ok) {
+                {
+                    const bool valid = o >= 0 && o < orows && col_ok;
                     const float mx = ap[slot].x, my = ap[slot].y;
                     const float vsum = __fsub_rn(as[slot].x, __fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)));
                     const float cxy = __fsub_rn(as[slot].y, __fmul_rn(mx, my));
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(MS_THREADS, 2)
                     const float num = __fmul_rn(__fadd_rn(__fmul_rn(2.0f * ux, uy), C1), __fadd_rn(2.0f * cxy, C2));
                     const float den = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), C1),
                                                 __fadd_rn(vsum, C2));
-                    csum += num == den ? 1.0f : __fdividef(num, den);
+                    const float ssim = num == den ? 1.0f : __fdividef(num, den);
+                    csum += valid ? ssim : 0.0f;   // a select: rows and columns outside add nothing
                 }
             }
             total += double(csum);
