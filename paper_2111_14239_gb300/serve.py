@@ -125,15 +125,19 @@ class Server:
 
     # ---- buffers --------------------------------------------------------------
     def _views(self, req: Request, base: int):
+        """Device and pinned-host views of a request's buffers.  Images use a 16-byte
+        row pitch; the host<->device copies move whole padded rows, so every copy is
+        one contiguous transfer from pinned memory (a strided view would make the
+        copy go through a pageable temporary and block the loop)."""
         h, w = req.image.shape
         ld = _align(w, 16)
         bi, br, bc = bytes_needed(h, w, req.r, self.n)
         oi, orc, oc = base, base + _align(bi), base + _align(bi) + _align(br)
-        d_in = self.d_arena[oi:oi + bi].view(h, ld)[:, :w]
-        d_rec = self.d_arena[orc:orc + br].view(h, ld)[:, :w]
+        d_in = self.d_arena[oi:oi + bi].view(h, ld)
+        d_rec = self.d_arena[orc:orc + br].view(h, ld)
         d_coef = self.d_arena[oc:oc + bc].view(torch.float32) if bc else None
-        h_in = self.h_arena[oi:oi + bi].view(h, ld)[:, :w]
-        h_rec = self.h_arena[orc:orc + br].view(h, ld)[:, :w]
+        h_in = self.h_arena[oi:oi + bi].view(h, ld)
+        h_rec = self.h_arena[orc:orc + br].view(h, ld)
         h_coef = self.h_arena[oc:oc + bc].view(torch.float32) if bc else None
         return d_in, d_rec, d_coef, h_in, h_rec, h_coef
 
@@ -184,9 +188,10 @@ class Server:
                 with torch.cuda.stream(s):
                     for req in batch:
                         d_in, d_rec, d_coef, h_in, h_rec, h_coef = req._slots["views"]
-                        h_in.copy_(torch.from_numpy(req.image))
-                        d_in.copy_(h_in, non_blocking=True)
-                        entries.append((d_in, req.plan, req.r, d_coef, d_rec))
+                        w = req.image.shape[1]
+                        h_in[:, :w].copy_(torch.from_numpy(req.image))
+                        d_in.copy_(h_in, non_blocking=True)          # whole padded rows: contiguous
+                        entries.append((d_in[:, :w], req.plan, req.r, d_coef, d_rec[:, :w]))
                     rklt_fused_items(make_items(entries), self.plans, sse, ps, stream=s)
                     for req in batch:
                         d_in, d_rec, d_coef, h_in, h_rec, h_coef = req._slots["views"]
@@ -212,7 +217,7 @@ class Server:
                         req.sse = float(sse_h[j])
                         if keep_outputs:
                             _, _, _, h_in, h_rec, h_coef = req._slots["views"]
-                            req.recon = h_rec.numpy().copy()
+                            req.recon = h_rec[:, :req.image.shape[1]].numpy().copy()
                             req.coef = h_coef.numpy().copy() if h_coef is not None else np.zeros(0, np.float32)
                         self.alloc.release(req._slots["off"], req._slots["need"])
                         req._slots = {}
