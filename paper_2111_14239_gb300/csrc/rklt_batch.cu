@@ -34,6 +34,39 @@ struct BatchItem {
     int out_index;      // position of this item in the caller's d_sse / d_psnr
 };
 
+// Last item whose unit range starts at or before u, searching forward from lo
+// (items[lo].unit_base <= u): a galloping step, then a binary search.
+__device__ __forceinline__ int item_of(const BatchItem *__restrict__ items, int nitems, int lo, int64_t u) {
+    int a = lo, step = 1, b = lo + 1;
+    while (b < nitems && items[b].unit_base <= u) {
+        a = b;
+        step <<= 1;
+        b = a + step;
+    }
+    int hi = (b < nitems ? b : nitems) - 1;
+    while (a < hi) {
+        const int mid = (a + hi + 1) >> 1;
+        if (items[mid].unit_base <= u) a = mid;
+        else hi = mid - 1;
+    }
+    return a;
+}
+
+// The pixels of lane's block of unit u (item it), or nothing past the image edge.
+template <int N>
+__device__ __forceinline__ bool load_unit(const BatchItem &it, int64_t u, int lane, uint32_t (&w)[N][N / 4], int &by,
+                                          int &bx) {
+    const int64_t local = u - it.unit_base;
+    by = int(local / it.units_x);
+    bx = int(local - int64_t(by) * it.units_x) * 32 + lane;
+    if (bx >= it.bw) return false;
+    load_block_words<N>(it.img + int64_t(by) * N * it.ld + bx * N, it.ld, w);
+    return true;
+}
+
+// Each warp walks units u = warp0, warp0 + nwarps, ...; the next unit's pixels are
+// loaded before the current unit is transformed, so each lane keeps two blocks'
+// loads in flight.
 template <int N, int D>
 __global__ void __launch_bounds__(256, 1)
     batch_kernel(const __grid_constant__ PlanK<N> P, const BatchItem *__restrict__ items, int nitems, int64_t nunits,
@@ -41,21 +74,26 @@ __global__ void __launch_bounds__(256, 1)
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    if (warp0 >= nunits) return;
+    int lo = item_of(items, nitems, 0, warp0);
+    BatchItem it = items[lo];
+    uint32_t w[N][N / 4];
+    int by = 0, bx = 0;
+    bool have = load_unit<N>(it, warp0, lane, w, by, bx);
     for (int64_t u = warp0; u < nunits; u += nwarps) {
-        int lo = 0, hi = nitems - 1;  // last item with unit_base <= u
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].unit_base <= u) lo = mid;
-            else hi = mid - 1;
+        // prefetch the next unit of this warp
+        const int64_t un = u + nwarps;
+        uint32_t wn[N][N / 4];
+        int lon = lo, byn = 0, bxn = 0;
+        bool haven = false;
+        BatchItem itn = it;
+        if (un < nunits) {
+            lon = item_of(items, nitems, lo, un);
+            if (lon != lo) itn = items[lon];
+            haven = load_unit<N>(itn, un, lane, wn, byn, bxn);
         }
-        const BatchItem it = items[lo];
-        const int64_t local = u - it.unit_base;
-        const int by = int(local / it.units_x);
-        const int bx = int(local - int64_t(by) * it.units_x) * 32 + lane;
         float sse = 0.0f;
-        if (bx < it.bw) {
-            uint32_t w[N][N / 4];
-            load_block_words<N>(it.img + int64_t(by) * N * it.ld + bx * N, it.ld, w);
+        if (have) {
             uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
             float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
             sse = block_core<N, D>(P, w, dst, it.ld_recon, it.r, coef, it.vec4 != 0, dst != nullptr);
@@ -63,6 +101,15 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
         if (lane == 0) partials[u] = sse;
+#pragma unroll
+        for (int k = 0; k < N; k++)
+#pragma unroll
+            for (int q = 0; q < N / 4; q++) w[k][q] = wn[k][q];
+        have = haven;
+        by = byn;
+        bx = bxn;
+        lo = lon;
+        it = itn;
     }
 }
 
