@@ -310,6 +310,7 @@ def run_ours(args):
     workloads = {}
     if world == 1 and not args.no_extras:
         for name, fn in (("single_512", lambda: leg_single(rk, dev, stream)),
+                         ("psnr_only_4096", lambda: leg_psnr_only(rk, d_img, dev, stream)),
                          ("comparison_klt_dct_4096", lambda: leg_comparison(rk, d_img, dev, stream)),
                          ("quant_jpeg_like_4096", lambda: leg_quant(rk, d_img, dev, stream)),
                          ("mssim_4096", lambda: leg_mssim(rk, d_img, dev, stream)),
@@ -380,6 +381,24 @@ def leg_single(rk, dev, stream):
     ms = _time_ms(lambda: rk.rklt_fused(plan, img, 10, sse, ps, zcoef=zc, recon=rec, stream=stream), 200, stream)
     return {"workload": "1 x 512x512, N=8, rho=0.95, r=10, fwd+zonal+inv+PSNR", "us_per_image": ms * 1e3,
             "mpixel_per_s": 512 * 512 / (ms / 1e3) / 1e6, "psnr_db": round(float(ps.item()), 4)}
+
+
+def leg_psnr_only(rk, d_img, dev, stream):
+    """The 16 x 4096^2 workload with PSNR as the only product (no coefficients, no
+    reconstruction): 1.0 B/px of algorithmic traffic, per N."""
+    import torch
+    nimg, H, W = d_img.shape
+    hbm, _ = peaks()
+    out = {"workload": f"{nimg} x {H}x{W} AR(1) rho={RHO}, N in {{4,8,16,32}}, r=N^2/8, PSNR only (1 B/px)"}
+    for n in NS:
+        plan = rk.rklt_make(n, RHO)
+        sse = torch.empty(nimg, dtype=torch.float64, device=dev)
+        ps = torch.empty(nimg, device=dev)
+        ms = _time_ms(lambda: rk.rklt_fused_batched(plan, d_img, n * n // 8, sse, ps, stream=stream), 10, stream)
+        gbs = nimg * H * W * 1.0 / (ms / 1e3) / 1e9
+        out[str(n)] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+                       "psnr_db_img0": round(float(ps[0].item()), 4)}
+    return out
 
 
 def leg_comparison(rk, d_img, dev, stream):
