@@ -59,6 +59,7 @@ constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchang
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
 constexpr int REG_DMAX8 = 5;     // N = 8: two-CTA register path up to this diagonal bound
 constexpr int REG8_FULL = 5;     // variant number of the N = 8 register path for any D (one CTA per SM)
+constexpr int REG_REAL = 6;      // variant number of the register path for real (exact KLT / DCT) plans
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
 constexpr int QV = 8;            // added to a variant number (N = 4, 8): quantised coefficients
 __host__ __device__ constexpr int vbase(int V) { return V & 7; }
@@ -97,7 +98,9 @@ __device__ __forceinline__ void load_block_words(const uint8_t *src, int64_t ld,
 // The whole per-block computation on a block held in registers (w); the 8-bit
 // reconstruction is written to dst (row stride ldd bytes) when recon is set.
 // FAST: coefficients and reconstruction both wanted (the branches resolved).
-template <int N, int D, bool Q = false, bool FAST = false>
+// REAL: a real (exact KLT / DCT) matrix: the column pass in FP32 instead of exact
+// binary16 sums of {0, +1, -1} entries.
+template <int N, int D, bool Q = false, bool FAST = false, bool REAL = false>
 __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&w)[N][N / 4], uint8_t *dst,
                                             int64_t ldd, int r, float *coef_, bool vec4, bool recon_) {
     float *coef = coef_;
@@ -106,7 +109,9 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
     constexpr int NP = N / 2;           // column pairs
     constexpr int DR = D < N ? D : N;   // rows / columns of C that carry retained terms
     constexpr int DA = DR > 0 ? DR : 1; // array extent (D = 0 keeps nothing)
-    constexpr bool FULL = D >= 2 * N - 1;  // every diagonal present: mask each entry by its zig-zag index
+    // every diagonal present, or one copy serving every D up to its own (real plans):
+    // mask each entry by its zig-zag index
+    constexpr bool FULL = D >= 2 * N - 1 || REAL;
     const __half2 k1024 = __float2half2_rn(1024.0f);
     // pixels (A[k][2p], A[k][2p+1]) of column pair p as exact binary16 pairs
     auto px = [&](int k, int p) -> __half2 {
@@ -114,22 +119,50 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
     };
     // column transform Y = T A (rows i < DR), two columns per instruction
     float Y[DA][N];
+    if constexpr (REAL) {
+        // FP32: mirrored sums / differences of the exact pixels, then the real
+        // entries of M as constant-bank FFMA operands
+        const float2 neg1f = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int p = 0; p < NP; p++) {
-        __half2 sp[H2], dp[H2];
+        for (int p = 0; p < NP; p++) {
+            float2 sp[H2], dp[H2];
 #pragma unroll
-        for (int j = 0; j < H2; j++) {
-            const __half2 top = px(j, p), bot = px(N - 1 - j, p);
-            sp[j] = __hadd2(top, bot);
-            dp[j] = __hsub2(top, bot);
+            for (int j = 0; j < H2; j++) {
+                const float2 top = __half22float2(px(j, p)), bot = __half22float2(px(N - 1 - j, p));
+                sp[j] = __fadd2_rn(top, bot);
+                dp[j] = __ffma2_rn(bot, neg1f, top);
+            }
+#pragma unroll
+            for (int i = 0; i < DR; i++) {
+                float ax = 0.0f, ay = 0.0f;
+#pragma unroll
+                for (int j = 0; j < H2; j++) {
+                    const float2 v = (i & 1) ? dp[j] : sp[j];
+                    ax = fmaf(P.T[i][j], v.x, ax);
+                    ay = fmaf(P.T[i][j], v.y, ay);
+                }
+                Y[i][2 * p] = ax;
+                Y[i][2 * p + 1] = ay;
+            }
         }
-#pragma unroll
-        for (int i = 0; i < DR; i++) {
-            __half2 acc = __hmul2(as_h2(P.T2[i][0]), (i & 1) ? dp[0] : sp[0]);
-#pragma unroll
-            for (int j = 1; j < H2; j++) acc = __hfma2(as_h2(P.T2[i][j]), (i & 1) ? dp[j] : sp[j], acc);
-            Y[i][2 * p] = __low2float(acc);
-            Y[i][2 * p + 1] = __high2float(acc);
+    } else {
+    #pragma unroll
+        for (int p = 0; p < NP; p++) {
+            __half2 sp[H2], dp[H2];
+    #pragma unroll
+            for (int j = 0; j < H2; j++) {
+                const __half2 top = px(j, p), bot = px(N - 1 - j, p);
+                sp[j] = __hadd2(top, bot);
+                dp[j] = __hsub2(top, bot);
+            }
+    #pragma unroll
+            for (int i = 0; i < DR; i++) {
+                __half2 acc = __hmul2(as_h2(P.T2[i][0]), (i & 1) ? dp[0] : sp[0]);
+    #pragma unroll
+                for (int j = 1; j < H2; j++) acc = __hfma2(as_h2(P.T2[i][j]), (i & 1) ? dp[j] : sp[j], acc);
+                Y[i][2 * p] = __low2float(acc);
+                Y[i][2 * p + 1] = __high2float(acc);
+            }
         }
     }
     // row transform: C = Y T^T on the support i + j < D; zonal mask on the last diagonal
@@ -260,12 +293,12 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 }
 
 // One block of a shared-memory tile, transformed in place.
-template <int N, int D, bool Q, bool FAST = false>
+template <int N, int D, bool Q, bool FAST = false, bool REAL = false>
 __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
                                            bool recon) {
     uint32_t w[N][N / 4];
     load_block_words<N>(blk, TW, w);
-    return block_core<N, D, Q, FAST>(P, w, blk, TW, r, coef, vec4, recon);
+    return block_core<N, D, Q, FAST, REAL>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
 struct TileCoord {
@@ -364,7 +397,7 @@ __device__ __forceinline__ float tile_reg8_full(const PlanK<8> &P, const FusedGe
 // The register path over one tile for a compile-time diagonal bound D: the bounds
 // test per block only on tiles that reach past the image, the coefficient base of
 // the image hoisted.
-template <int N, int D, bool Q, bool FAST>
+template <int N, int D, bool Q, bool FAST, bool REAL>
 __device__ __forceinline__ float tile_reg_d(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
@@ -381,46 +414,48 @@ __device__ __forceinline__ float tile_reg_d(const PlanK<N> &P, const FusedGeom &
         const int gy = tc.ty * (TH / N) + by, gx = tc.tx * BPR + bx;
         if (!full && (gy * N >= g.H || gx * N >= g.W)) continue;
         float *coef = zimg ? zimg + (int64_t(gy) * bw + gx) * r : nullptr;
-        sse += block_reg<N, D, Q, FAST>(P, tile + by * N * TW + bx * N, r, coef, vec4, recon);
+        sse += block_reg<N, D, Q, FAST, REAL>(P, tile + by * N * TW + bx * N, r, coef, vec4, recon);
     }
     return sse;
 }
 
-template <int N, bool Q, bool FAST>
+template <int N, bool Q, bool FAST, bool REAL>
 __device__ __forceinline__ float tile_reg_f(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct) {
-    if constexpr (N == 4) {
+    if constexpr (REAL) {  // one copy for every D it serves (N = 4: all; N = 8: D <= REG_DMAX8)
+        return tile_reg_d<N, (N == 4 ? 2 * N - 1 : REG_DMAX8), Q, FAST, true>(P, g, tile, tc, ct);
+    } else if constexpr (N == 4) {
         switch (g.D) {
-            case 0: return tile_reg_d<4, 0, Q, FAST>(P, g, tile, tc, ct);
-            case 1: return tile_reg_d<4, 1, Q, FAST>(P, g, tile, tc, ct);
-            case 2: return tile_reg_d<4, 2, Q, FAST>(P, g, tile, tc, ct);
-            case 3: return tile_reg_d<4, 3, Q, FAST>(P, g, tile, tc, ct);
-            case 4: return tile_reg_d<4, 4, Q, FAST>(P, g, tile, tc, ct);
-            case 5: return tile_reg_d<4, 5, Q, FAST>(P, g, tile, tc, ct);
-            case 6: return tile_reg_d<4, 6, Q, FAST>(P, g, tile, tc, ct);
-            default: return tile_reg_d<4, 7, Q, FAST>(P, g, tile, tc, ct);
+            case 0: return tile_reg_d<4, 0, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 1: return tile_reg_d<4, 1, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 2: return tile_reg_d<4, 2, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 3: return tile_reg_d<4, 3, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 4: return tile_reg_d<4, 4, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 5: return tile_reg_d<4, 5, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 6: return tile_reg_d<4, 6, Q, FAST, REAL>(P, g, tile, tc, ct);
+            default: return tile_reg_d<4, 7, Q, FAST, REAL>(P, g, tile, tc, ct);
         }
     } else {
         switch (g.D) {
-            case 0: return tile_reg_d<N, 0, Q, FAST>(P, g, tile, tc, ct);
-            case 1: return tile_reg_d<N, 1, Q, FAST>(P, g, tile, tc, ct);
-            case 2: return tile_reg_d<N, 2, Q, FAST>(P, g, tile, tc, ct);
-            case 3: return tile_reg_d<N, 3, Q, FAST>(P, g, tile, tc, ct);
-            case 4: return tile_reg_d<N, 4, Q, FAST>(P, g, tile, tc, ct);
-            default: return tile_reg_d<N, 5, Q, FAST>(P, g, tile, tc, ct);
+            case 0: return tile_reg_d<N, 0, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 1: return tile_reg_d<N, 1, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 2: return tile_reg_d<N, 2, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 3: return tile_reg_d<N, 3, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 4: return tile_reg_d<N, 4, Q, FAST, REAL>(P, g, tile, tc, ct);
+            default: return tile_reg_d<N, 5, Q, FAST, REAL>(P, g, tile, tc, ct);
         }
     }
 }
 
 // The D dispatch happens once per tile; the benchmark configuration (coefficients
 // and reconstruction, no quantiser) runs a copy with those branches resolved.
-template <int N, bool Q>
+template <int N, bool Q, bool REAL = false>
 __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
-    if constexpr (!Q && N == 4) {
-        if (g.zcoef != nullptr && g.recon != nullptr) return tile_reg_f<N, false, true>(P, g, tile, tc, ct);
+    if constexpr (!Q && !REAL && N == 4) {
+        if (g.zcoef != nullptr && g.recon != nullptr) return tile_reg_f<N, false, true, false>(P, g, tile, tc, ct);
     }
-    return tile_reg_f<N, Q, false>(P, g, tile, tc, ct);
+    return tile_reg_f<N, Q, false, REAL>(P, g, tile, tc, ct);
 }
 
 // ---------------------------------------------------------------------------
@@ -808,8 +843,8 @@ __host__ __device__ inline int fused_variant(int N, int D) {
 // Variant for a real (exact KLT / DCT) plan: only the FP32 paths, since the register
 // and tensor-core paths rely on T having entries in {0, +1, -1}.
 __host__ __device__ inline int real_variant(int N, int D) {
-    if (N == 4) return 1;
-    if (N == 8) return D <= 4 ? 2 : 1;
+    if (N == 4) return REG_REAL;
+    if (N == 8) return D <= REG_DMAX8 ? REG_REAL : 1;
     const int Dr = D < N ? D : N;
     return Dr <= N / 4 ? 1 : (Dr <= N / 2 ? 2 : 3);
 }
@@ -825,6 +860,7 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         constexpr bool Q = V >= QV;
         constexpr int VB = vbase(V);
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
+        else if constexpr (VB == REG_REAL) return tile_reg<N, false, true>(P, g, tile, tc, ct);
         else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg8_full<Q>(P, g, tile, tc, ct, Zs);
         else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
@@ -1230,14 +1266,14 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     if constexpr (N == 4) {
         switch (V) {
             case 0: fn = reinterpret_cast<const void *>(fused_kernel<4, 0>); break;
-            case 1: fn = reinterpret_cast<const void *>(fused_kernel<4, 1>); break;
+            case REG_REAL: fn = reinterpret_cast<const void *>(fused_kernel<4, REG_REAL>); break;
             default: fn = reinterpret_cast<const void *>(fused_kernel<4, QV>); break;
         }
     } else if constexpr (N == 8) {
         switch (V) {
             case 0: fn = reinterpret_cast<const void *>(fused_kernel<8, 0>); break;
             case 1: fn = reinterpret_cast<const void *>(fused_kernel<8, 1>); break;
-            case 2: fn = reinterpret_cast<const void *>(fused_kernel<8, 2>); break;
+            case REG_REAL: fn = reinterpret_cast<const void *>(fused_kernel<8, REG_REAL>); break;
             case REG8_FULL: fn = reinterpret_cast<const void *>(fused_kernel<8, REG8_FULL>); break;
             case QV: fn = reinterpret_cast<const void *>(fused_kernel<8, QV>); break;
             default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + REG8_FULL>); break;
