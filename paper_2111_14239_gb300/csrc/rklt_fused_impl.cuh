@@ -592,7 +592,7 @@ __device__ __forceinline__ float tile_coop(const PlanK<N> &P, const FusedGeom &g
 }
 
 // ---------------------------------------------------------------------------
-// Cooperative path for N = 8, 16 and 32.  All block-rows of the tile (R = 64/N of
+// Cooperative path for N = 16 and 32.  All block-rows of the tile (R = 64/N of
 // them, NB = 256/N blocks each) are transformed together in three phases
 // separated by barriers:
 //   1. column pass: a thread takes two adjacent columns of one block-row and forms
@@ -828,8 +828,8 @@ namespace rklt {
 //   REG8_FULL (the register path for the full block, one CTA per SM);
 //   N = 32 with D <= 16, N = 16 with D <= 8: TC_V (tensor cores);
 //   N >= 16 otherwise: 1, 2, 3 = cooperative path (all block-rows at once) sized for
-//   Dr <= N/4, N/2, N;  N = 8, real plans with D <= 4: 2 = the same path for Dr <= 4;
-//   N = 4, 8 otherwise: 1 = cooperative path block-row by block-row.
+//   Dr <= N/4, N/2, N;  real (exact KLT / DCT) plans: REG_REAL for N = 4 and for N = 8
+//   with D <= REG_DMAX8, else 1 = cooperative path block-row by block-row.
 // QV is added for the quantised form (N = 4, 8).
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
@@ -862,7 +862,6 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
         else if constexpr (VB == REG_REAL) return tile_reg<N, false, true>(P, g, tile, tc, ct);
         else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg8_full<Q>(P, g, tile, tc, ct, Zs);
-        else if constexpr (N == 8 && VB == 2) return tile_coop2<8, 4, Q>(P, g, tile, tc, ct, Ys, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
         if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tc, ct, Ys, Zs);
@@ -949,7 +948,7 @@ __host__ __device__ inline SmemLayout smem_layout(int stages, int r, int D, int 
     int ys = 0, zs = 0;
     if (V == TC_V) {
         zs = (NCONS_TC / 32) * TC_ZS * 4 + TC_TAB_BYTES;
-    } else if (N >= 16 || V == 2) {  // all block-rows at once
+    } else if (N >= 16) {  // all block-rows at once
         const int Dr = D < N ? D : N;
         ys = (TH / N) * Dr * (TW / N) * (N + 4) * 4;
         zs = coop2_stage_coef(N, r) ? (TH / N) * (TW / N) * (r | 1) * 4 : 0;
@@ -1260,7 +1259,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    g.stages = swz ? 6 : ((N >= 16 || vbase(V) == 2) ? 3 : 4);
+    g.stages = swz ? 6 : (N >= 16 ? 3 : 4);
     const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, vbase(V));
     const void *fn = nullptr;
     if constexpr (N == 4) {
