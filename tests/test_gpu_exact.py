@@ -68,7 +68,8 @@ def test_fused_exact_transforms(rk, orc, n, kind):
     zz = orc.zigzag(n)
     d = torch.from_numpy(img).cuda()
     nblk = (H // n) * (W // n)
-    for r in sorted({1, max(1, n * n // 8), n * n // 2}):
+    # r = 15 at N = 8 is the largest support of the register path (diagonals 0..4)
+    for r in sorted({1, max(1, n * n // 8), min(15, n * n), n * n // 2, n * n}):
         for transport in (0, 1):
             zc = torch.full((nblk, r), float("nan"), device="cuda")
             rec = torch.zeros_like(d)
