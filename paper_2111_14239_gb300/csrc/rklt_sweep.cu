@@ -11,9 +11,10 @@
 // the parity structure of the KLT rows (H[a][b] = 0 when a + b is odd), so pairs
 // with i_k + i_l or j_k + j_l odd are skipped at compile time.
 //
-// One CTA per (image, distinct T): each thread takes blocks of the image, keeps
-// its N*N - 1 running sums in registers, and the CTA adds them in a fixed order
-// (FP64), so each image's values do not depend on the rest of the batch.
+// One CTA per (image, chunk of SWEEP_CHUNK blocks) and distinct T: each thread takes
+// blocks of the chunk, keeps its N*N - 1 running sums in registers, and the CTA adds
+// them in a fixed order (FP64); the chunks of an image are then summed in order, so
+// each image's values do not depend on the rest of the batch.
 #include <algorithm>
 #include <vector>
 
@@ -34,6 +35,22 @@ struct ZZTab {
 };
 template <int N>
 __device__ constexpr ZZTab<N> kZZ{};
+
+// Zig-zag positions split by (row parity, column parity), ascending.  G_kl is zero
+// unless k and l share both parities, so the Gram sums stay inside one class.
+template <int N>
+struct ZZClass {
+    int idx[4][N * N / 4];
+    constexpr ZZClass() : idx() {
+        int n[4] = {0, 0, 0, 0};
+        for (int k = 0; k < N * N; k++) {
+            const int q = (zz_row(N, k) & 1) * 2 + (zz_col(N, k) & 1);
+            idx[q][n[q]++] = k;
+        }
+    }
+};
+template <int N>
+__device__ constexpr ZZClass<N> kCls{};
 
 template <int N>
 struct SweepK {
@@ -89,37 +106,56 @@ __device__ __forceinline__ void block_forward_full(const SweepK<N> &P, const uin
     }
 }
 
-// grid: (nimg, ndistinct); block: 256 threads; dynamic smem: 256 * (N*N - 1) floats.
+constexpr int SWEEP_CHUNK = 1024;  // blocks per CTA (4 per thread): short waves, a small tail
+
+// grid: (nimg, nchunk), one launch per distinct T; block: 256 threads; dynamic smem:
+// 256 * (N*N - 1) floats.  sse_out: [image][chunk][distinct T][N*N].
 template <int N>
 __global__ void __launch_bounds__(256, 1)
     sweep_kernel(const __grid_constant__ SweepK<N> P, const uint8_t *__restrict__ imgs, int H, int W, int64_t ld,
                  int64_t img_stride, int tslot, int ntslots, double *__restrict__ sse_out) {
     constexpr int K = N * N;
     extern __shared__ float red[];  // [blockDim.x][K - 1]
-    const int img = blockIdx.x;
+    const int img = blockIdx.x, chunk = blockIdx.y, nchunk = gridDim.y;
     const uint8_t *base = imgs + int64_t(img) * img_stride;
     const int bw = W / N, nblk = (H / N) * bw;
+    const int b_end = min(nblk, (chunk + 1) * SWEEP_CHUNK);
     float acc[K - 1];
 #pragma unroll
     for (int q = 0; q < K - 1; q++) acc[q] = 0.0f;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    for (int b = chunk * SWEEP_CHUNK + int(threadIdx.x); b < b_end; b += blockDim.x) {
         const int by = b / bw, bx = b - by * bw;
         uint32_t w[N][N / 4];
         load_block_words<N>(base + int64_t(by) * N * ld + bx * N, ld, w);
         float c[K];
         block_forward_full<N>(P, w, c);
+        // v_k = c_k (c_k G_kk + 2 sum_{l > k} c_l G_kl), written over c_k: within a
+        // class, member a reads only members b > a, so c_k is no longer needed once
+        // its own v_k is formed (every index below is a compile-time constant)
+        constexpr int M = K / 4;
+        if (!P.orthogonal) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+#pragma unroll
+                for (int a = 0; a < M; a++) {
+                    const int ka = kCls<N>.idx[q][a];
+                    float t = 0.0f;
+#pragma unroll
+                    for (int b = a + 1; b < M; b++) {
+                        const int kb = kCls<N>.idx[q][b];
+                        t = fmaf(c[kb], P.G[ka][kb], t);
+                    }
+                    c[ka] = c[ka] * fmaf(c[ka], P.G[ka][ka], 2.0f * t);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) c[k] = c[k] * (c[k] * P.G[k][k]);
+        }
         float run = 0.0f;  // SSE(r) for the current r, from r = K - 1 down to 1
 #pragma unroll
         for (int rr = K - 1; rr >= 1; rr--) {
-            float t = 0.0f;
-            if (!P.orthogonal) {
-#pragma unroll
-                for (int l = rr + 1; l < K; l++) {
-                    if (((kZZ<N>.row[rr] + kZZ<N>.row[l]) & 1) == 0 && ((kZZ<N>.col[rr] + kZZ<N>.col[l]) & 1) == 0)
-                        t = fmaf(c[l], P.G[rr][l], t);
-                }
-            }
-            run = fmaf(c[rr], fmaf(c[rr], P.G[rr][rr], 2.0f * t), run);
+            run += c[rr];
             acc[rr - 1] += run;  // keep the first rr coefficients
         }
     }
@@ -130,20 +166,21 @@ __global__ void __launch_bounds__(256, 1)
     for (int q = threadIdx.x; q < K - 1; q += blockDim.x) {
         double s = 0.0;
         for (int t = 0; t < int(blockDim.x); t++) s += double(red[t * (K - 1) + q]);
-        sse_out[(int64_t(img) * ntslots + tslot) * K + q] = s;
+        sse_out[((int64_t(img) * nchunk + chunk) * ntslots + tslot) * K + q] = s;
     }
-    if (threadIdx.x == 0) sse_out[(int64_t(img) * ntslots + tslot) * K + (K - 1)] = 0.0;  // r = N*N keeps all
+    if (threadIdx.x == 0) sse_out[((int64_t(img) * nchunk + chunk) * ntslots + tslot) * K + (K - 1)] = 0.0;  // r = N*N
 }
 
 // Scatter per-distinct-T SSE to the callers' [image][plan][r] layout with PSNR.
-__global__ void sweep_scatter(const double *__restrict__ sse_t, int nimg, int ntslots, const int *__restrict__ slot_of,
-                              int nplans, int K, int64_t npx, double *sse, float *psnr) {
+__global__ void sweep_scatter(const double *__restrict__ sse_t, int nimg, int nchunk, int ntslots,
+                              const int *__restrict__ slot_of, int nplans, int K, int64_t npx, double *sse, float *psnr) {
     const int64_t total = int64_t(nimg) * nplans * K;
     for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
         const int r = int(q % K);
         const int64_t ip = q / K;
         const int p = int(ip % nplans), img = int(ip / nplans);
-        const double s = sse_t[(int64_t(img) * ntslots + slot_of[p]) * K + r];
+        double s = 0.0;  // the image's chunks in order
+        for (int c = 0; c < nchunk; c++) s += sse_t[((int64_t(img) * nchunk + c) * ntslots + slot_of[p]) * K + r];
         if (sse) sse[q] = s;
         float v;
         if (npx == 0) v = __int_as_float(0x7fc00000);
@@ -187,7 +224,9 @@ rklt_status launch_sweep(const std::vector<const Plan *> &distinct, const std::v
     const int nt = int(distinct.size());
     cudaMemPool_t pool = scratch_pool();
     if (!pool) return fail(RKLT_ERR_CUDA, "could not create the scratch memory pool");
-    const size_t tb = size_t(nimg) * nt * K * sizeof(double);
+    const int nblk = (H / N) * (W / N);
+    const int nchunk = std::max(1, (nblk + SWEEP_CHUNK - 1) / SWEEP_CHUNK);
+    const size_t tb = size_t(nimg) * nchunk * nt * K * sizeof(double);
     const size_t sb = slot_of.size() * sizeof(int);
     void *scratch = nullptr;
     if (cudaMallocFromPoolAsync(&scratch, tb + sb, pool, st) != cudaSuccess)
@@ -204,15 +243,15 @@ rklt_status launch_sweep(const std::vector<const Plan *> &distinct, const std::v
     std::vector<unsigned char> blob;
     for (int t = 0; t < nt && e == cudaSuccess; t++) {
         fill_sweep<N>(*distinct[t], blob);
-        sweep_kernel<N><<<nimg, threads, smem, st>>>(*reinterpret_cast<const SweepK<N> *>(blob.data()), d_imgs, H, W,
-                                                     ld, istride, t, nt, sse_t);
+        sweep_kernel<N><<<dim3(nimg, nchunk), threads, smem, st>>>(*reinterpret_cast<const SweepK<N> *>(blob.data()),
+                                                                   d_imgs, H, W, ld, istride, t, nt, sse_t);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         const int64_t total = int64_t(nimg) * slot_of.size() * K;
         const unsigned grid = unsigned(std::min<int64_t>((total + 255) / 256, 4096));
-        sweep_scatter<<<grid, 256, 0, st>>>(sse_t, nimg, nt, d_slot, int(slot_of.size()), K, int64_t(H) * W, d_sse,
-                                            d_psnr);
+        sweep_scatter<<<grid, 256, 0, st>>>(sse_t, nimg, nchunk, nt, d_slot, int(slot_of.size()), K, int64_t(H) * W,
+                                            d_sse, d_psnr);
         e = cudaGetLastError();
     }
     cudaFreeAsync(scratch, st);
