@@ -109,13 +109,13 @@ __device__ __forceinline__ void block_forward_full(const SweepK<N> &P, const uin
 constexpr int SWEEP_CHUNK = 1024;  // blocks per CTA (4 per thread): short waves, a small tail
 
 // grid: (nimg, nchunk), one launch per distinct T; block: 256 threads; dynamic smem:
-// 256 * (N*N - 1) floats.  sse_out: [image][chunk][distinct T][N*N].
+// 8 warps * (N*N - 1) floats.  sse_out: [image][chunk][distinct T][N*N].
 template <int N>
 __global__ void __launch_bounds__(256, 1)
     sweep_kernel(const __grid_constant__ SweepK<N> P, const uint8_t *__restrict__ imgs, int H, int W, int64_t ld,
                  int64_t img_stride, int tslot, int ntslots, double *__restrict__ sse_out) {
     constexpr int K = N * N;
-    extern __shared__ float red[];  // [blockDim.x][K - 1]
+    extern __shared__ float red[];  // [warps][K - 1]
     const int img = blockIdx.x, chunk = blockIdx.y, nchunk = gridDim.y;
     const uint8_t *base = imgs + int64_t(img) * img_stride;
     const int bw = W / N, nblk = (H / N) * bw;
@@ -159,13 +159,19 @@ __global__ void __launch_bounds__(256, 1)
             acc[rr - 1] += run;  // keep the first rr coefficients
         }
     }
-    float *mine = red + threadIdx.x * (K - 1);
+    // per warp: a fixed xor-butterfly in FP32; then the warps in order in FP64
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 #pragma unroll
-    for (int q = 0; q < K - 1; q++) mine[q] = acc[q];
+    for (int q = 0; q < K - 1; q++) {
+        float v = acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp * (K - 1) + q] = v;
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < K - 1; q += blockDim.x) {
         double s = 0.0;
-        for (int t = 0; t < int(blockDim.x); t++) s += double(red[t * (K - 1) + q]);
+        for (int t = 0; t < nwarp; t++) s += double(red[t * (K - 1) + q]);
         sse_out[((int64_t(img) * nchunk + chunk) * ntslots + tslot) * K + q] = s;
     }
     if (threadIdx.x == 0) sse_out[((int64_t(img) * nchunk + chunk) * ntslots + tslot) * K + (K - 1)] = 0.0;  // r = N*N
@@ -235,7 +241,7 @@ rklt_status launch_sweep(const std::vector<const Plan *> &distinct, const std::v
     int *d_slot = reinterpret_cast<int *>(static_cast<char *>(scratch) + tb);
     cudaError_t e = cudaMemcpyAsync(d_slot, slot_of.data(), sb, cudaMemcpyHostToDevice, st);
     const int threads = 256;
-    const size_t smem = size_t(threads) * (K - 1) * sizeof(float);
+    const size_t smem = size_t(threads / 32) * (K - 1) * sizeof(float);
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(sweep_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
