@@ -52,48 +52,74 @@ __device__ __forceinline__ int item_of(const BatchItem *__restrict__ items, int 
     return a;
 }
 
-// The pixels of lane's block of unit u (item it), or nothing past the image edge.
-template <int N>
-__device__ __forceinline__ bool load_unit(const BatchItem &it, int64_t u, int lane, uint32_t (&w)[N][N / 4], int &by,
-                                          int &bx) {
+// Asynchronous copies global -> shared (cp.async, cached in L1 and L2).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// Position of lane's block in unit u of item it; false past the image's right edge.
+__device__ __forceinline__ bool unit_block(const BatchItem &it, int64_t u, int lane, int &by, int &bx) {
     const int64_t local = u - it.unit_base;
     by = int(local / it.units_x);
     bx = int(local - int64_t(by) * it.units_x) * 32 + lane;
-    if (bx >= it.bw) return false;
-    load_block_words<N>(it.img + int64_t(by) * N * it.ld + bx * N, it.ld, w);
-    return true;
+    return bx < it.bw;
+}
+
+// Stage lane's block (N rows of N bytes) into dst with asynchronous copies; row k
+// goes to dst + k * 32 N, so that the 32 lanes' rows are contiguous.
+template <int N>
+__device__ __forceinline__ void stage_block(const BatchItem &it, int by, int bx, uint8_t *dst) {
+    const uint8_t *src = it.img + int64_t(by) * N * it.ld + bx * N;
+#pragma unroll
+    for (int k = 0; k < N; k++) cp_async<N>(dst + k * 32 * N, src + k * it.ld);
 }
 
 // Each warp walks units u = warp0, warp0 + nwarps, ...; the next unit's pixels are
-// loaded before the current unit is transformed, so each lane keeps two blocks'
-// loads in flight.
+// copied into the warp's other shared-memory buffer (cp.async) while the current
+// unit is transformed, so the loads of one unit overlap the arithmetic of the last.
+// Dynamic shared memory: warps x 2 slots x N rows x 32 lanes x N bytes.
 template <int N, int D>
 __global__ void __launch_bounds__(256, 1)
     batch_kernel(const __grid_constant__ PlanK<N> P, const BatchItem *__restrict__ items, int nitems, int64_t nunits,
                  float *__restrict__ partials) {
+    extern __shared__ __align__(16) uint8_t bsm[];
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     if (warp0 >= nunits) return;
+    uint8_t *mine = bsm + int(threadIdx.x >> 5) * (2 * 32 * N * N) + lane * N;  // slot s at + s * 32 * N * N
     int lo = item_of(items, nitems, 0, warp0);
     BatchItem it = items[lo];
-    uint32_t w[N][N / 4];
     int by = 0, bx = 0;
-    bool have = load_unit<N>(it, warp0, lane, w, by, bx);
+    bool have = unit_block(it, warp0, lane, by, bx);
+    if (have) stage_block<N>(it, by, bx, mine);
+    cp_async_commit();
+    int slot = 0;
     for (int64_t u = warp0; u < nunits; u += nwarps) {
-        // prefetch the next unit of this warp
+        // start the next unit's copies into the other slot
         const int64_t un = u + nwarps;
-        uint32_t wn[N][N / 4];
         int lon = lo, byn = 0, bxn = 0;
         bool haven = false;
         BatchItem itn = it;
         if (un < nunits) {
             lon = item_of(items, nitems, lo, un);
             if (lon != lo) itn = items[lon];
-            haven = load_unit<N>(itn, un, lane, wn, byn, bxn);
+            haven = unit_block(itn, un, lane, byn, bxn);
+            if (haven) stage_block<N>(itn, byn, bxn, mine + (slot ^ 1) * 32 * N * N);
         }
+        cp_async_commit();
+        cp_async_wait<1>();  // this unit's copies (the older group) have landed
         float sse = 0.0f;
         if (have) {
+            uint32_t w[N][N / 4];
+            load_block_words<N>(mine + slot * 32 * N * N, 32 * N, w);
             uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
             float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
             sse = block_core<N, D>(P, w, dst, it.ld_recon, it.r, coef, it.vec4 != 0, dst != nullptr);
@@ -101,16 +127,14 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
         if (lane == 0) partials[u] = sse;
-#pragma unroll
-        for (int k = 0; k < N; k++)
-#pragma unroll
-            for (int q = 0; q < N / 4; q++) w[k][q] = wn[k][q];
+        slot ^= 1;
         have = haven;
         by = byn;
         bx = bxn;
         lo = lon;
         it = itn;
     }
+    cp_async_wait<0>();
 }
 
 // One CTA per item: FP64 sum of its unit partials in order, then PSNR.
@@ -222,6 +246,9 @@ const void *pick_fn(int D, std::integer_sequence<int, Ds...>) {
     return tab[D];
 }
 
+// Dynamic shared memory of a batch launch: two staging slots per warp.
+size_t batch_smem(int N, int threads) { return size_t(threads / 32) * 2 * 32 * N * N; }
+
 const void *batch_kernel_for(int N, int D) {
     return N == 4 ? pick_fn<4>(D, std::make_integer_sequence<int, 8>{})
                   : pick_fn<8>(D, std::make_integer_sequence<int, 16>{});
@@ -235,7 +262,7 @@ cudaError_t launch_group(int N, const Group &g, const BatchItem *d_items, float 
         const void *fn = batch_kernel_for(N, g.D);
         const void *kp = g.plan->k.data();
         void *args[] = {const_cast<void *>(kp), &d_items, const_cast<int *>(&nitems), &nunits, &partials};
-        const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, st);
+        const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, batch_smem(N, threads), st);
         if (e != cudaSuccess) return e;
     }
     batch_finalize<<<nitems, 256, 0, st>>>(d_items, nitems, nunits, partials, sse, psnr);
@@ -247,7 +274,8 @@ int grid_for(int N, int threads, int per_sm, int64_t nunits) {
     int dev = 0;
     cudaGetDevice(&dev);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_for(N, N == 4 ? 7 : 15), threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_for(N, N == 4 ? 7 : 15), threads,
+                                                  batch_smem(N, threads));
     const int use = std::max(1, std::min(per_sm, occ));
     const int64_t warps_needed = nunits;
     const int64_t ctas_needed = (warps_needed * 32 + threads - 1) / threads;
