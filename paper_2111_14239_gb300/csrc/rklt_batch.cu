@@ -295,6 +295,11 @@ struct rklt_batch {
     int threads = 256, per_sm = 1;
     double tuned_us = 0.0;
     cudaStream_t stream = nullptr;
+    // the groups fan out over side streams (fork on one event, join on one per stream),
+    // so that one group's last wave overlaps the next groups' launches
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -310,18 +315,43 @@ void batch_free(rklt_batch *b) {
     for (auto p : b->d_items) cudaFree(p);
     for (auto p : b->d_partials) cudaFree(p);
     if (b->stream) cudaStreamDestroy(b->stream);
+    for (auto s : b->side) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
+constexpr int kBatchSideStreams = 4;
+
+// Groups go round-robin over the side streams, largest first (the groups are
+// independent: each has its own items, partials and outputs).
 cudaError_t batch_enqueue(rklt_batch *b, int threads, int per_sm, cudaStream_t st) {
-    for (size_t gi = 0; gi < b->groups.size(); gi++) {
-        const Group &g = b->groups[gi];
-        const int grid = grid_for(b->N, threads, per_sm, g.nunits);
-        const cudaError_t e =
-            launch_group(b->N, g, b->d_items[gi], b->d_partials[gi], b->sse, b->psnr, threads, grid, st);
+    const bool fan = !b->side.empty();
+    cudaError_t e = cudaSuccess;
+    if (fan) {
+        e = cudaEventRecord(b->fork, st);
+        for (size_t k = 0; k < b->side.size() && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    std::vector<size_t> order(b->groups.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return b->groups[x].nunits > b->groups[y].nunits; });
+    for (size_t k = 0; k < order.size(); k++) {
+        const size_t gi = order[k];
+        const Group &g = b->groups[gi];
+        const int grid = grid_for(b->N, threads, per_sm, g.nunits);
+        const cudaStream_t s = fan ? b->side[k % b->side.size()] : st;
+        e = launch_group(b->N, g, b->d_items[gi], b->d_partials[gi], b->sse, b->psnr, threads, grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (fan) {
+        for (size_t k = 0; k < b->side.size() && e == cudaSuccess; k++) {
+            e = cudaEventRecord(b->join[k], b->side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[k], 0);
+        }
+    }
+    return e;
 }
 
 }  // namespace
@@ -371,6 +401,15 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
     b->sse = d_sse;
     b->psnr = d_psnr;
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchSideStreams && e == cudaSuccess; k++) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t j = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->side.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(j);
+    }
     for (const Group &g : b->groups) {
         if (e != cudaSuccess) break;
         BatchItem *di = nullptr;
