@@ -274,8 +274,7 @@ int grid_for(int N, int threads, int per_sm, int64_t nunits) {
     int dev = 0;
     cudaGetDevice(&dev);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_for(N, N == 4 ? 7 : 15), threads,
-                                                  batch_smem(N, threads));
+    occ = occupancy(batch_kernel_for(N, N == 4 ? 7 : 15), threads, batch_smem(N, threads));
     const int use = std::max(1, std::min(per_sm, occ));
     const int64_t warps_needed = nunits;
     const int64_t ctas_needed = (warps_needed * 32 + threads - 1) / threads;

@@ -3,8 +3,10 @@
 #include <cudaTypedefs.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <utility>
 
 #include "rklt_internal.h"
@@ -63,6 +65,21 @@ int ensure_smem_attr(const void *kernel) {
     if (done.insert({dev, kernel}).second)
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     return dev;
+}
+
+int occupancy(const void *kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, kernel, threads, smem);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto f = cache.find(key);
+    if (f != cache.end()) return f->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) n = 0;
+    cache.emplace(key, n);
+    return n;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

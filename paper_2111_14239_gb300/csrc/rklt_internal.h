@@ -106,6 +106,7 @@ rklt_status cuda_fail(cudaError_t err, const char *what);
 cudaMemPool_t scratch_pool();                 // per-device stream-ordered pool for library scratch
 int sm_count(int dev);
 int ensure_smem_attr(const void *kernel);     // opt in to 227 KB dynamic smem; returns the device
+int occupancy(const void *kernel, int threads, size_t smem);  // resident CTAs per SM (cached per device)
 // 3-D tensor map over nimg images of W x H bytes; swizzle128 selects the 128-byte
 // swizzled shared-memory layout (box_w must then be 128).
 bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64_t ld, int64_t stride,
