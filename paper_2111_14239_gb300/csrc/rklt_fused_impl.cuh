@@ -222,24 +222,31 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
         }
     }
     // inverse row transform: X[i][l] = sum_j C[i][j] T^{-1}[l][j]  (i < DR)
+    // (j outer, l inner: each C'[i][j] is formed once and feeds the H2 sums; every
+    // sum still runs over j in ascending order)
     float X[DA][N];
 #pragma unroll
     for (int i = 0; i < DR; i++) {
+        float e[H2], o[H2];
 #pragma unroll
-        for (int l = 0; l < H2; l++) {
-            float e = 0.0f, o = 0.0f;
+        for (int l = 0; l < H2; l++) e[l] = o[l] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < DR; j++) {
-                if (i + j < D) {
-                    float cm;
-                    if constexpr (Q) cm = Bq[i][j] * P.qt[i][j];
-                    else cm = Cm[i][j];
-                    if (j & 1) o = fmaf(cm, P.Ti[l][j], o);
-                    else e = fmaf(cm, P.Ti[l][j], e);
+        for (int j = 0; j < DR; j++) {
+            if (i + j < D) {
+                float cm;
+                if constexpr (Q) cm = Bq[i][j] * P.qt[i][j];
+                else cm = Cm[i][j];
+#pragma unroll
+                for (int l = 0; l < H2; l++) {
+                    if (j & 1) o[l] = fmaf(cm, P.Ti[l][j], o[l]);
+                    else e[l] = fmaf(cm, P.Ti[l][j], e[l]);
                 }
             }
-            X[i][l] = e + o;
-            X[i][N - 1 - l] = e - o;
+        }
+#pragma unroll
+        for (int l = 0; l < H2; l++) {
+            X[i][l] = e[l] + o[l];
+            X[i][N - 1 - l] = e[l] - o[l];
         }
     }
     // inverse column transform A'[k][c] = sum_i T^{-1}[k][i] X[i][c], one mirrored row
