@@ -263,3 +263,23 @@ def test_bounded_wait_gives_up(rk):
     rk.rklt_fused(plan, img, 10, sse, ps)
     rk.rklt_device_status()
     assert sse.item() == 0.0
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
+def test_output_subsets_agree(rk, n):
+    """Every subset of the optional outputs (coefficients, 8-bit reconstruction) gives
+    the same SSE / PSNR and the same coefficients / reconstruction as the full call:
+    the kernels take separate code paths for the full set and the others."""
+    H, W = SHAPES[n]
+    img = si.ar1_image(H, W, 0.9, 31 + n)
+    plan = rk.rklt_make(n, 0.95)
+    r = n * n // 8
+    full = run_fused(rk, plan, img, r, pitch=((W + 15) // 16) * 16)
+    for want_coef, want_recon in ((True, False), (False, True), (False, False)):
+        zc, rec, sse, ps = run_fused(rk, plan, img, r, pitch=((W + 15) // 16) * 16, want_coef=want_coef,
+                                     want_recon=want_recon)
+        assert sse == full[2] and ps == full[3]
+        if want_coef:
+            assert np.array_equal(zc, full[0])
+        if want_recon:
+            assert np.array_equal(rec, full[1])
