@@ -237,8 +237,10 @@ typedef struct rklt_item {
  * (warp per unit, each lane one block, coalesced row accesses), then a per-image
  * SSE / PSNR kernel.  d_sse[i], d_psnr[i] receive item i's results; they are
  * bit-identical to what a batch of item i alone produces.  Scratch (descriptors,
- * per-unit partials) comes from a stream-ordered pool.  h_items may be reused as
- * soon as the call returns.
+ * per-unit partials) comes from a stream-ordered pool; the descriptors travel
+ * through a library-owned pinned ring (4 MB per device, reused once the copy
+ * that read a region has completed), so the call does not wait for work already
+ * queued.  h_items may be reused as soon as the call returns.
  * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED (N not 4 or 8,
  * misaligned rows), RKLT_ERR_OOM, RKLT_ERR_CUDA. */
 rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,

@@ -14,6 +14,8 @@
 // rklt_batch_* builds the queue once, captures the launches in a CUDA graph
 // and picks the launch shape with a small autotuner (timed candidates).
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 #include <map>
 #include <utility>
 #include <vector>
@@ -353,6 +355,73 @@ cudaError_t batch_enqueue(rklt_batch *b, int threads, int per_sm, cudaStream_t s
     return e;
 }
 
+// Pinned staging for the item descriptors of immediate launches.  A copy from
+// pageable memory would be staged by the runtime, and once its staging buffers are
+// busy the host waits for earlier copies, which wait for the kernels queued before
+// them: the request loop would stall behind work already on the GPU.  The ring is
+// reused in order; a region is handed out again only after the event recorded
+// behind its copy has completed.
+class ItemRing {
+  public:
+    static constexpr size_t kBytes = size_t(4) << 20;
+    // A pinned region of `bytes` (<= kBytes) for a copy enqueued on `st`; the caller
+    // fills it, enqueues the copy and then calls done(st).  Null if no pinned memory.
+    void *get(size_t bytes) {
+        if (!base_ && cudaHostAlloc(&base_, kBytes, cudaHostAllocDefault) != cudaSuccess) base_ = nullptr;
+        if (!base_ || bytes > kBytes) return nullptr;
+        bytes = (bytes + 255) & ~size_t(255);
+        for (;;) {
+            if (used_ == 0) head_ = 0;  // empty: start over at the front
+            // live regions occupy [head_ - used_, head_) in ring order; allocate after them
+            size_t off = head_;
+            if (off + bytes > kBytes) off = 0;  // wrap: never split a region
+            const size_t skip = (off == 0 && head_ != 0) ? kBytes - head_ : 0;
+            if (used_ + skip + bytes <= kBytes) {
+                used_ += skip + bytes;
+                pending_ = {off, skip + bytes};
+                head_ = off + bytes;
+                return static_cast<char *>(base_) + off;
+            }
+            if (regions_.empty()) return nullptr;
+            cudaEventSynchronize(regions_.front().ev);  // the oldest copy has read its bytes
+            release_front();
+        }
+    }
+    void done(cudaStream_t st) {
+        cudaEvent_t ev = nullptr;
+        if (!free_ev_.empty()) {
+            ev = free_ev_.back();
+            free_ev_.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            ev = nullptr;
+        }
+        if (ev) cudaEventRecord(ev, st);
+        regions_.push_back({pending_.first, pending_.second, ev});
+        while (!regions_.empty() && (!regions_.front().ev || cudaEventQuery(regions_.front().ev) == cudaSuccess))
+            release_front();
+    }
+
+  private:
+    struct Region {
+        size_t off, len;
+        cudaEvent_t ev;
+    };
+    void release_front() {
+        const Region r = regions_.front();
+        regions_.erase(regions_.begin());
+        used_ -= r.len;
+        if (r.ev) free_ev_.push_back(r.ev);
+    }
+    void *base_ = nullptr;
+    size_t head_ = 0, used_ = 0;
+    std::pair<size_t, size_t> pending_{0, 0};
+    std::vector<Region> regions_;
+    std::vector<cudaEvent_t> free_ev_;
+};
+
+std::mutex g_ring_mu;
+ItemRing g_ring[64];  // per device
+
 }  // namespace
 
 extern "C" {
@@ -375,8 +444,25 @@ rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *c
             return fail(RKLT_ERR_OOM, "scratch allocation failed");
         BatchItem *d_items = static_cast<BatchItem *>(scratch);
         float *partials = reinterpret_cast<float *>(static_cast<char *>(scratch) + ib);
-        // pageable source: the runtime stages it before returning, so g.items may go away
-        cudaError_t e = cudaMemcpyAsync(d_items, g.items.data(), ib, cudaMemcpyHostToDevice, st);
+        // descriptors through the pinned ring (an asynchronous copy); pageable if it is full
+        cudaError_t e = cudaSuccess;
+        {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            std::lock_guard<std::mutex> lk(g_ring_mu);
+            ItemRing &ring = g_ring[dev >= 0 && dev < 64 ? dev : 0];
+            // under stream capture the copy would run at replay, after the region is reused
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(st, &cs);
+            void *pinned = cs == cudaStreamCaptureStatusNone ? ring.get(ib) : nullptr;
+            if (pinned) {
+                std::memcpy(pinned, g.items.data(), ib);
+                e = cudaMemcpyAsync(d_items, pinned, ib, cudaMemcpyHostToDevice, st);
+                ring.done(st);
+            } else {
+                e = cudaMemcpyAsync(d_items, g.items.data(), ib, cudaMemcpyHostToDevice, st);
+            }
+        }
         if (e == cudaSuccess)
             e = launch_group(N, g, d_items, partials, d_sse, d_psnr, 256, grid_for(N, 256, 1, g.nunits), st);
         cudaFreeAsync(scratch, st);
