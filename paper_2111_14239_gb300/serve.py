@@ -19,6 +19,8 @@ host) and throughput.
 from __future__ import annotations
 
 import bisect
+import contextlib
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -26,6 +28,24 @@ import numpy as np
 import torch
 
 from . import Plan, make_items, rklt_fused, rklt_fused_items, rklt_make
+
+
+@contextlib.contextmanager
+def frozen_heap():
+    """Move every object alive on entry into the collector's permanent generation
+    until exit.  A full collection during a request loop then scans only objects
+    made inside the loop; scanning the whole heap (the trace, the image pool,
+    torch's objects) stalls the loop for tens of milliseconds, which lands in
+    the latency of every request waiting meanwhile.  A heap that was already
+    partly frozen on entry stays frozen on exit (no partial unfreeze exists)."""
+    was_frozen = gc.get_freeze_count() > 0
+    gc.collect()
+    gc.freeze()
+    try:
+        yield
+    finally:
+        if not was_frozen:
+            gc.unfreeze()
 
 
 def _align(x: int, a: int = 256) -> int:
@@ -149,6 +169,10 @@ class Server:
     # ---- continuous batching --------------------------------------------------
     def run(self, trace: list, keep_outputs: bool = False, max_batch: int = 256) -> dict:
         """Replay `trace` (list of Request, sorted by arrival) in real time."""
+        with frozen_heap():
+            return self._run(trace, keep_outputs, max_batch)
+
+    def _run(self, trace: list, keep_outputs: bool, max_batch: int) -> dict:
         max_batch = min(max_batch, self.max_batch)
         pending = list(trace)
         waiting: list = []
@@ -239,6 +263,11 @@ class Server:
 def serve_plain(plans: list, trace: list, device="cuda", keep_outputs: bool = False) -> dict:
     """One request at a time: copy in, one rklt_fused launch, copy out, synchronise.
     Staging and device buffers are preallocated for the largest request."""
+    with frozen_heap():
+        return _serve_plain(plans, trace, device, keep_outputs)
+
+
+def _serve_plain(plans: list, trace: list, device, keep_outputs: bool) -> dict:
     dev = torch.device(device)
     s = torch.cuda.Stream(dev)
     n = plans[0].N

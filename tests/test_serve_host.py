@@ -1,4 +1,5 @@
-"""Host logic of the serving loop (no GPU): the first-fit arena allocator."""
+"""Host logic of the serving loop (no GPU): the first-fit arena allocator and the
+frozen-heap scope around request loops."""
 import random
 
 import pytest
@@ -36,3 +37,28 @@ def test_arena_random_churn_never_overlaps():
     for o, n in list(live.items()):
         a.release(o, n)
     assert a.free == [(0, 1 << 16)]
+
+
+def test_frozen_heap_scope():
+    import gc
+    saved = gc.get_freeze_count()
+    gc.unfreeze()
+    try:
+        keep = [[i] for i in range(1000)]
+        with serve.frozen_heap():
+            assert gc.get_freeze_count() >= len(keep)
+            assert gc.isenabled()
+        assert gc.get_freeze_count() == 0
+        with pytest.raises(RuntimeError):
+            with serve.frozen_heap():
+                raise RuntimeError("the heap is unfrozen on the way out")
+        assert gc.get_freeze_count() == 0
+        # a heap frozen by someone else stays frozen
+        gc.freeze()
+        with serve.frozen_heap():
+            pass
+        assert gc.get_freeze_count() > 0
+    finally:
+        gc.unfreeze()
+        if saved:
+            gc.freeze()
