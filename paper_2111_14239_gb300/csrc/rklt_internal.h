@@ -35,6 +35,14 @@ struct PlanK {
     static constexpr int QN = N <= 8 ? N : 1;
     float qw[QN][QN];      // fl32(s_i s_j / Q_ij): Bbar = floor(fl32(C qw) + 1/2)
     float qt[QN][QN];      // fl32(Q_ij / (s_i s_j)): the dequantised value in the C domain
+    // Parseval form of a rounded plan whose T T^T is diagonal (N <= 8; zero otherwise).
+    // With d_i = (T T^T)_ii, m = lcm(d_0 .. d_{N-1}) and e_i = m / d_i, T^{-1} =
+    // T^T diag(1/d), so a block's error is sum a^2 - sum_retained C_ij^2 / (d_i d_j)
+    // = (m^2 sum a^2 - sum_retained pw_ij C_ij^2) / m^2 with pw_ij = e_i e_j: integers.
+    static constexpr int PN = N <= 8 ? N : 1;
+    int32_t pw[PN][PN];
+    int32_t pm2;           // m^2; 0 when the plan has no Parseval form
+    float pinv;            // fl32(1 / m^2)
 };
 
 // Host-side plan object behind the opaque rklt_plan handle.

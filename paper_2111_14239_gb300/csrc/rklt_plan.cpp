@@ -6,6 +6,7 @@
 // parameters.  K is the Markov-1 KLT of Sec. 2.1 in closed form.
 #include <atomic>
 #include <cmath>
+#include <numeric>
 #include <cstring>
 #include <new>
 
@@ -131,6 +132,21 @@ void fill_kparams(Plan &p) {
             const uint32_t h = t == 0 ? 0x0000u : (t > 0 ? 0x3C00u : 0xBC00u);
             k.T2[i][j] = h | (h << 16);
         }
+    // Parseval weights (rounded plans with T T^T diagonal, N <= 8)
+    if constexpr (M <= 8) {
+        if (p.kind == 0 && p.orthogonal) {
+            long d[M], m = 1;
+            for (int i = 0; i < M; i++) {
+                d[i] = 0;
+                for (int j = 0; j < M; j++) d[i] += long(p.T[size_t(i) * M + j]) * p.T[size_t(i) * M + j];
+                m = std::lcm(m, d[i]);
+            }
+            for (int i = 0; i < M; i++)
+                for (int j = 0; j < M; j++) k.pw[i][j] = int32_t((m / d[i]) * (m / d[j]));
+            k.pm2 = int32_t(m * m);   // d_i <= M <= 8: m <= 840, m^2 <= 705600
+            k.pinv = float(1.0 / double(m * m));
+        }
+    }
 }
 
 rklt_status fill_tables(Plan &p) {

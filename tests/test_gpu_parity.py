@@ -265,21 +265,85 @@ def test_bounded_wait_gives_up(rk):
     assert sse.item() == 0.0
 
 
+def zz_diagonals(n, r):
+    """Anti-diagonals i + j < D touched by the first r zig-zag positions."""
+    D, cnt = 0, 0
+    while cnt < r:
+        cnt += min(D, 2 * n - 2 - D) + 1
+        D += 1
+    return D
+
+
+def parseval_path(plan, r):
+    """Whether a call without reconstruction takes the integer-Parseval register copy:
+    a rounded plan with T T^T diagonal on the register path (N = 4; N = 8 with D <= 5)."""
+    return plan.kind == 0 and plan.orthogonal and (plan.N == 4 or (plan.N == 8 and zz_diagonals(8, r) <= 5))
+
+
 @pytest.mark.parametrize("n", [4, 8, 16, 32])
-def test_output_subsets_agree(rk, n):
+def test_output_subsets_agree(rk, orc, n):
     """Every subset of the optional outputs (coefficients, 8-bit reconstruction) gives
-    the same SSE / PSNR and the same coefficients / reconstruction as the full call:
-    the kernels take separate code paths for the full set and the others."""
+    the same coefficients / reconstruction as the full call, and the same SSE / PSNR
+    bit for bit whenever the reconstruction is formed: the kernels take separate code
+    paths for the full set and the others.  Without a reconstruction, plans with
+    T T^T diagonal take the error from Parseval's identity in integers; that SSE is
+    checked against the oracle and against the full call's."""
     H, W = SHAPES[n]
     img = si.ar1_image(H, W, 0.9, 31 + n)
     plan = rk.rklt_make(n, 0.95)
     r = n * n // 8
     full = run_fused(rk, plan, img, r, pitch=((W + 15) // 16) * 16)
+    ref = orc.pipeline(n, orc.Plan(n, 0.95).That, img, r)[0]
     for want_coef, want_recon in ((True, False), (False, True), (False, False)):
         zc, rec, sse, ps = run_fused(rk, plan, img, r, pitch=((W + 15) // 16) * 16, want_coef=want_coef,
                                      want_recon=want_recon)
-        assert sse == full[2] and ps == full[3]
+        if not want_recon and parseval_path(plan, r):
+            check_sse(sse, ref, H, W, n)
+            assert abs(sse - full[2]) <= 2 * SSE_REL * ref and abs(ps - full[3]) <= 2e-3
+        else:
+            assert sse == full[2] and ps == full[3]
         if want_coef:
             assert np.array_equal(zc, full[0])
         if want_recon:
             assert np.array_equal(rec, full[1])
+
+
+@pytest.mark.parametrize("n,rho", [(4, 0.3), (4, 0.95), (8, 0.2), (8, 0.95)])
+def test_parseval_no_recon(rk, orc, n, rho):
+    """Calls without a reconstruction on plans with T T^T diagonal: the SSE is the
+    block energy less the retained C^2 / (d_i d_j), in integers.  Against the oracle
+    over every r the register path serves, on a ragged image in both transports;
+    r = N^2 must give exactly 0 and r = 0 the image energy; the coefficients are
+    bit-identical to the full call's."""
+    H, W = SHAPES[n]
+    img = si.ar1_image(H, W, 0.9, 41 + n)
+    plan = rk.rklt_make(n, rho)
+    assert plan.orthogonal
+    p = orc.Plan(n, rho)
+    energy = float(np.sum(img.astype(np.float64) ** 2))
+    pitch = ((W + 15) // 16) * 16      # aligned: the TMA ring (transport 0) and plain loads (1)
+    for r in ([0, 1, 2, 3, 5, 8, 11, 15, 16] if n == 4 else [0, 1, 3, 6, 8, 10, 13, 15]):
+        assert parseval_path(plan, r)
+        for transport in (0, 1):
+            zc, _, sse, ps = run_fused(rk, plan, img, r, pitch=pitch, want_recon=False, transport=transport)
+            if r == 0:
+                assert sse == pytest.approx(energy, rel=1e-6)   # FP32 sums of exact block energies
+                continue
+            ref, zref, _ = orc.pipeline(n, p.That, img, r, want_coef=True)
+            if r == n * n:
+                assert sse == 0.0 and ps == math.inf
+            else:
+                check_sse(sse, ref, H, W, n)
+                assert abs(ps - 10 * math.log10(255 ** 2 * H * W / ref)) <= 1e-3
+            check_coef(zc, zref)
+            full = run_fused(rk, plan, img, r, pitch=pitch, transport=transport)
+            assert np.array_equal(zc, full[0])
+    # a constant image at r = 1: where the oracle's error is zero (every AC row of T
+    # sums to zero) the integer form gives exactly zero and PSNR +inf
+    flat = np.full((H, W), 77, np.uint8)
+    _, _, sse, ps = run_fused(rk, plan, flat, 1, want_recon=False)
+    ref = orc.pipeline(n, p.That, flat, 1)[0]
+    if ref <= 1e-9 * float(np.sum(flat.astype(np.float64) ** 2)):
+        assert sse == 0.0 and ps == math.inf
+    else:
+        check_sse(sse, ref, H, W, n)

@@ -97,6 +97,37 @@ def test_parseval_orthogonal(orc, rho):
         assert sse == pytest.approx(np.sum(B[:, r:] ** 2), rel=1e-9, abs=1e-6)
 
 
+@pytest.mark.parametrize("n,rho", [(4, 0.3), (4, 0.95), (8, 0.2), (8, 0.95)])
+def test_parseval_retained_integer_form(orc, n, rho):
+    """T T^T = diag(d): T^-1 = T^T diag(1/d), so the error of keeping r coefficients
+    is the block energy less the retained C_ij^2 / (d_i d_j).  With m = lcm(d) every
+    m^2 / (d_i d_j) is an integer and the sum is exact in integers; the oracle's FP64
+    reconstruction error must agree.  (The no-reconstruction kernels use this form.)"""
+    import fractions
+    p = orc.Plan(n, rho)
+    assert p.orthogonal
+    d = [int(x) for x in np.sum(p.T.astype(np.int64) ** 2, axis=1)]
+    m = math.lcm(*d)
+    assert all((m * m) % (di * dj) == 0 for di in d for dj in d)
+    img = si.ar1_image(3 * n, 5 * n, 0.9, 17)
+    C = orc.int_stage(n, p.T, img)
+    zr, zc = orc.zigzag(n)
+    blocks = img.reshape(3, n, 5, n).transpose(0, 2, 1, 3).reshape(-1, n, n).astype(np.int64)
+    energy = int(np.sum(blocks ** 2))
+    for r in (0, 1, 2, n * n // 8, n * n // 2 + 1, n * n - 1, n * n):
+        kept = sum(int(Cb[zr[k], zc[k]]) ** 2 * (m * m // (d[zr[k]] * d[zc[k]])) for Cb in C for k in range(r))
+        exact = fractions.Fraction(m * m * energy - kept, m * m)
+        assert exact >= 0
+        if r == 0:
+            assert exact == energy
+            continue
+        sse, _, _ = orc.pipeline(n, p.That, img, r)
+        if r == n * n:
+            assert exact == 0 and sse < 1e-12 * energy
+        else:
+            assert sse == pytest.approx(float(exact), rel=1e-10)
+
+
 @pytest.mark.parametrize("n,rho", [(8, 0.5), (8, 0.7), (16, 0.95)])
 def test_gram_error_non_orthogonal(orc, n, rho):
     """Non-orthogonal T: A - A' = T^-1 E T^-T with E the discarded integer
