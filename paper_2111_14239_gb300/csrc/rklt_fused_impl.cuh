@@ -1321,7 +1321,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (V == TC_V) fn = reinterpret_cast<const void *>(fused_kernel<N, TC_V>);
     }
     const int dev = ensure_smem_attr(fn);
-        const int threads = (V == TC_V ? NCONS_TC : NCONS) + 32;
+    const int threads = (V == TC_V ? NCONS_TC : NCONS) + 32;
     int per_sm = occupancy(fn, threads, L.total);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(g.ntiles, int64_t(per_sm) * sm_count(dev));
