@@ -383,7 +383,9 @@ class ItemRing {
                 return static_cast<char *>(base_) + off;
             }
             if (regions_.empty()) return nullptr;
-            cudaEventSynchronize(regions_.front().ev);  // the oldest copy has read its bytes
+            // the oldest copy has read its bytes (a region without an event was
+            // copied synchronously in done())
+            if (regions_.front().ev) cudaEventSynchronize(regions_.front().ev);
             release_front();
         }
     }
@@ -395,7 +397,11 @@ class ItemRing {
         } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
             ev = nullptr;
         }
-        if (ev) cudaEventRecord(ev, st);
+        if (ev && cudaEventRecord(ev, st) != cudaSuccess) {
+            free_ev_.push_back(ev);
+            ev = nullptr;
+        }
+        if (!ev) cudaStreamSynchronize(st);  // untracked: let the copy finish before reuse
         regions_.push_back({pending_.first, pending_.second, ev});
         while (!regions_.empty() && (!regions_.front().ev || cudaEventQuery(regions_.front().ev) == cudaSuccess))
             release_front();
