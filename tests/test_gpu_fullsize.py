@@ -4,7 +4,8 @@ one image at a time, plus properties that hold at any size.
 
   16 x 4096^2, N in {4, 8, 16, 32}, r = N^2/8 (one batched fused launch per N):
       sampled blocks -> integer stage recovered bit-exact from the coefficients,
-      coefficients, 8-bit reconstruction; every image's SSE / PSNR;
+      coefficients, 8-bit reconstruction; every image's SSE / PSNR, with all
+      outputs and with PSNR only;
   one 512^2 image, N = 8, r = 10: the whole output;
   r-sweep of 256 x 512^2 over the ten grid plans: every image and plan at r = 10, 37
       (and at r = 1, 63 for three images), r = 64 exactly lossless;
@@ -72,11 +73,21 @@ def test_roofline_workload(rk, orc, roofline, n):
         C = orc.int_stage(n, p.T, blk)[0][zr[:r], zcol[:r]]
         assert np.array_equal(np.rint(got / sij).astype(np.int64), C)
         check_recon_u8(rec[i, by * n:(by + 1) * n, bx * n:(bx + 1) * n].cpu().numpy(), rref, n)
+    # PSNR only, the launch the PSNR-only benchmark line times (N = 4, 8 at rho = 0.95:
+    # the Parseval copy; N = 16, 32: the inverse), against the same references
+    sse1 = torch.empty(nimg, dtype=torch.float64, device="cuda")
+    ps1 = torch.empty(nimg, device="cuda")
+    rk.rklt_fused_batched(plan, d, r, sse1, ps1)
+    torch.cuda.synchronize()
+    rk.rklt_device_status()
     sse_h, ps_h = sse.cpu().numpy(), ps.cpu().numpy()
+    sse1_h, ps1_h = sse1.cpu().numpy(), ps1.cpu().numpy()
     for i in range(nimg):
         ref, _, _ = orc.pipeline(n, p.That, imgs[i], r)
-        check_sse(sse_h[i], ref, H, W, n)
-        assert abs(ps_h[i] - 10 * math.log10(255 ** 2 * H * W / ref)) <= 1e-3
+        psnr_ref = 10 * math.log10(255 ** 2 * H * W / ref)
+        for s_, p_ in ((sse_h[i], ps_h[i]), (sse1_h[i], ps1_h[i])):
+            check_sse(s_, ref, H, W, n)
+            assert abs(p_ - psnr_ref) <= 1e-3
 
 
 def test_single_512_whole_output(rk, orc):
