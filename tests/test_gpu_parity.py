@@ -192,6 +192,12 @@ def test_batched_equals_single(rk, n):
         assert np.array_equal(zc[i].cpu().numpy(), z1)
         assert np.array_equal(rec[i].cpu().numpy(), r1)
         assert sse[i].item() == s1 and ps[i].item() == p1
+    # PSNR only (the Parseval copy for N = 4, 8): also identical alone and in the batch
+    rk.rklt_fused_batched(plan, d, r, sse, ps)
+    torch.cuda.synchronize()
+    for i in range(3):
+        _, _, s1, p1 = run_fused(rk, plan, imgs[i], r, want_coef=False, want_recon=False)
+        assert sse[i].item() == s1 and ps[i].item() == p1
 
 
 def test_edge_cases(rk, orc):
