@@ -150,14 +150,16 @@ rklt_status rklt_plan_info(const rklt_plan *plan, int8_t *h_T, double *h_s, int 
  * Split path (Sec. 4.1): forward -> zonal -> inverse -> psnr.
  * ------------------------------------------------------------------------ */
 
-/* Exact integer stage C = T A T^T of every block, int32, raster order inside a
+/* Exact integer stage C = T A T^T of every block (Sec. 2.3 with Eq. 2's integer T,
+ * applied to disjoint blocks as in Sec. 4.1), int32, raster order inside a
  * block: d_C[blk][i][j] (N*N per block).  |C| <= (nnz per row)^2 * 255.
  * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
 rklt_status rklt_forward_int(const rklt_plan *plan, const uint8_t *d_img, int H, int W,
                              int64_t ld, int32_t *d_C, void *stream);
 
-/* Normalised forward transform B = That A That^T = (s s^T) o C of every block,
- * FP32, zig-zag order: d_coef[blk][z] with z = 0..N*N-1.
+/* Normalised forward transform B = That A That^T = (s s^T) o C of every block
+ * (Eq. 1 for S, Sec. 4.1 and the Appendix for the 2-D form), FP32, zig-zag order:
+ * d_coef[blk][z] with z = 0..N*N-1.
  * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
 rklt_status rklt_forward(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld,
                          float *d_coef, void *stream);
@@ -204,7 +206,8 @@ rklt_status rklt_fused(const rklt_plan *plan, const uint8_t *d_img, int H, int W
                        float *d_zcoef, uint8_t *d_recon, int64_t ld_recon, double *d_sse,
                        float *d_psnr, void *stream);
 
-/* nimg images of one shape in one launch.  Image i starts at d_img + i*img_stride
+/* rklt_fused (Sec. 4.1, Appendix) over nimg images of one shape in one launch
+ * (the batched form of the per-image pass).  Image i starts at d_img + i*img_stride
  * (bytes); its reconstruction at d_recon + i*recon_stride; its coefficients after
  * those of images 0..i-1; d_sse[i], d_psnr[i] are its scalars.  When the base
  * pointers and pitches are 16-byte aligned the tiles move by TMA (bulk tensor
@@ -236,8 +239,9 @@ typedef struct rklt_item {
     int64_t ld_recon;
 } rklt_item;
 
-/* Immediate batched pass: items are grouped by plan; per group one launch of a
- * persistent kernel over a flattened queue of 32-block units of all its images
+/* Immediate batched pass: rklt_fused (Sec. 4.1, Appendix) for images of uneven
+ * sizes, each with its own plan and r.  Items are grouped by plan; per group one
+ * launch of a persistent kernel over a flattened queue of 32-block units of all its images
  * (warp per unit, each lane one block, coalesced row accesses), then a per-image
  * SSE / PSNR kernel.  d_sse[i], d_psnr[i] receive item i's results; they are
  * bit-identical to what a batch of item i alone produces.  Scratch (descriptors,
@@ -252,9 +256,9 @@ rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *c
 
 typedef struct rklt_batch rklt_batch;
 
-/* A reusable batch: the work queue (library-owned device memory, freed by
- * rklt_batch_destroy) is built once, the launch sequence is captured into a CUDA
- * graph and every rklt_batch_run replays it.  The device buffers named in h_items
+/* A reusable batch of rklt_fused_items work (Sec. 4.1 per image): the work queue
+ * (library-owned device memory, freed by rklt_batch_destroy) is built once, the
+ * launch sequence is captured into a CUDA graph and every rklt_batch_run replays it.  The device buffers named in h_items
  * and d_sse / d_psnr are baked into the graph: refill them between runs, keep
  * them alive until rklt_batch_destroy.  flags bit 0 = autotune: time a few launch
  * shapes (threads per CTA, CTAs per SM) on the batch itself and keep the fastest;
