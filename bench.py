@@ -36,12 +36,13 @@ NIMG, SIDE = 16, 4096
 # keyed by kernel; None until a capture of the current kernel exists.
 # The fused kernel instantiation the library picks for r = N^2/8 (variant 0: one thread
 # per block; 4: tensor cores, one warp per 32 x 32 block or region).
-KERNEL = {4: "fused_kernel<4, 0>", 8: "fused_kernel<8, 0>", 16: "fused_kernel<16, 4>", 32: "fused_kernel<32, 4>"}
+# (N = 4, 8: the register path with the error by Parseval, pars_kernel<N, D, OUT> with
+# D the diagonal bound of r = N^2/8 and OUT = 3 (coefficients and reconstruction);
+# N = 16, 32: the tensor-core variant of fused_kernel.)
+KERNEL = {4: "pars_kernel<4, 2, 3>", 8: "pars_kernel<8, 4, 3>", 16: "fused_kernel<16, 4>", 32: "fused_kernel<32, 4>"}
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
     # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
-    "fused_kernel<4, 0>": 268508160 + 343627264,
-    "fused_kernel<8, 0>": 268548096 + 346659328,
     "fused_kernel<16, 4>": 268536576 + 339311872,
     "fused_kernel<32, 4>": 268518144 + 342444544,
 }

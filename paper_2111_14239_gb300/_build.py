@@ -7,6 +7,7 @@ entry point.
 from __future__ import annotations
 
 import os
+import re
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -18,7 +19,8 @@ LIB = os.path.join(OUT_DIR, "librklt.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = [
-    "rklt_fused_n8.cu", "rklt_fused_n32.cu", "rklt_fused_n16.cu", "rklt_fused_n4.cu",
+    "rklt_fused_n8.cu", "rklt_fused_n32.cu", "rklt_fused_n16.cu", "rklt_fused_n4.cu", "rklt_reg_n8.cu",
+    "rklt_reg_n8b.cu", "rklt_reg_n4.cu",
     "rklt_batch.cu", "rklt_sweep.cu", "rklt_split.cu", "rklt_noalloc.cu", "rklt_quant.cu", "rklt_mssim.cu",
     "rklt_plan.cpp",
     "rklt_host.cpp", "rklt_capi.cpp",
@@ -38,6 +40,27 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _tu_deps(src: str) -> set:
+    """The source file and every quoted include it reaches (paths resolved next to the includer)."""
+    seen, todo = set(), [os.path.join(CSRC, src)]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in seen or not os.path.exists(f):
+            continue
+        seen.add(f)
+        with open(f, encoding="utf-8") as fh:
+            for inc in _INCLUDE_RE.findall(fh.read()):
+                todo.append(os.path.join(os.path.dirname(f), inc))
+    return seen
+
+
+def _obj_current(src: str, obj: str) -> bool:
+    return os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in _tu_deps(src))
+
+
 def up_to_date() -> bool:
     return os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime()
 
@@ -51,6 +74,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src: str):
         obj = os.path.join(OUT_DIR, src + ".o")
+        if not force and not ptxas_info and _obj_current(src, obj):
+            return src, obj, subprocess.CompletedProcess([], 0, "", "")
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info and src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]

@@ -27,6 +27,7 @@ rklt_status fused_common(const rklt_plan *plan, FusedArgs &a, void *stream) {
     }
     if (!empty && (int64_t(a.H) * a.W) / int64_t(a.H) != a.W) return fail(RKLT_ERR_SHAPE, "image too large");
     a.force_plain = transport_mode() == 1;
+    a.engine = tensor_engine();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (N) {
         case 4: return launch_fused_n4(plan->p, a, st);
@@ -70,7 +71,8 @@ rklt_status rklt_device_status(void) {
     const cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     unsigned int v = take_status_n4() | take_status_n8() | take_status_n16() | take_status_n32() | take_status_split() |
-                     take_status_mssim();
+                     take_status_mssim() | take_status_reg_n4() | take_status_reg_n8() |
+                     take_status_reg_n8b();
     if (v) return fail(RKLT_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return RKLT_OK;
 }

@@ -60,7 +60,6 @@ static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_i
 constexpr int REG_DMAX8 = 5;     // N = 8: two-CTA register path up to this diagonal bound
 constexpr int REG8_FULL = 5;     // variant number of the N = 8 register path for any D (one CTA per SM)
 constexpr int REG_REAL = 6;      // variant number of the register path for real (exact KLT / DCT) plans
-constexpr int REG_PARS = 7;      // register path without reconstruction, error by Parseval (T T^T diagonal)
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
 constexpr int QV = 8;            // added to a variant number (N = 4, 8): quantised coefficients
 __host__ __device__ constexpr int vbase(int V) { return V & 7; }
@@ -101,9 +100,9 @@ __device__ __forceinline__ void load_block_words(const uint8_t *src, int64_t ld,
 // FAST: coefficients and reconstruction both wanted (the branches resolved).
 // REAL: a real (exact KLT / DCT) matrix: the column pass in FP32 instead of exact
 // binary16 sums of {0, +1, -1} entries.
-// PARS: no reconstruction wanted and T T^T diagonal: the error comes from Parseval's
-// identity in exact integers instead of an inverse transform (P.pm2 != 0).
-template <int N, int D, bool Q = false, bool FAST = false, bool REAL = false, bool PARS = false>
+// (Rounded plans with T T^T diagonal run the register path of rklt_reg.cuh, which
+// takes the error from Parseval's identity; this one serves the others.)
+template <int N, int D, bool Q = false, bool FAST = false, bool REAL = false>
 __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&w)[N][N / 4], uint8_t *dst,
                                             int64_t ldd, int r, float *coef_, bool vec4, bool recon_) {
     float *coef = coef_;
@@ -224,26 +223,6 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
             }
         }
     }
-    if constexpr (PARS && !Q && !REAL && !FAST) {
-        // T^{-1} = T^T diag(1/d): the error of the block is its pixel energy less the
-        // retained C_ij^2 / (d_i d_j), scaled by m^2 into integers (|C| < 2^15, so C^2
-        // fits in 32 bits; the sums in 64).  Exact up to the one final rounding.
-        uint32_t sa = 0;
-#pragma unroll
-        for (int k = 0; k < N; k++)
-#pragma unroll
-            for (int q = 0; q < N / 4; q++) sa = __dp4a(w[k][q], w[k][q], sa);
-        unsigned long long kept = 0;  // unsigned: one wide multiply-add per term
-#pragma unroll
-        for (int i = 0; i < DR; i++)
-#pragma unroll
-            for (int j = 0; j < DR; j++)
-                if (i + j < D) {
-                    const int c = __float2int_rn(Cm[i][j]);
-                    kept += static_cast<unsigned long long>(uint32_t(c * c)) * uint32_t(P.pw[i][j]);
-                }
-        return __ull2float_rn(static_cast<unsigned long long>(uint32_t(P.pm2)) * sa - kept) * P.pinv;
-    }
     // inverse row transform: X[i][l] = sum_j C[i][j] T^{-1}[l][j]  (i < DR)
     // (j outer, l inner: each C'[i][j] is formed once and feeds the H2 sums; every
     // sum still runs over j in ascending order)
@@ -323,12 +302,12 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
 }
 
 // One block of a shared-memory tile, transformed in place.
-template <int N, int D, bool Q, bool FAST = false, bool REAL = false, bool PARS = false>
+template <int N, int D, bool Q, bool FAST = false, bool REAL = false>
 __device__ __forceinline__ float block_reg(const PlanK<N> &P, uint8_t *blk, int r, float *coef, bool vec4,
                                            bool recon) {
     uint32_t w[N][N / 4];
     load_block_words<N>(blk, TW, w);
-    return block_core<N, D, Q, FAST, REAL, PARS>(P, w, blk, TW, r, coef, vec4, recon);
+    return block_core<N, D, Q, FAST, REAL>(P, w, blk, TW, r, coef, vec4, recon);
 }
 
 struct TileCoord {
@@ -427,7 +406,7 @@ __device__ __forceinline__ float tile_reg8_full(const PlanK<8> &P, const FusedGe
 // The register path over one tile for a compile-time diagonal bound D: the bounds
 // test per block only on tiles that reach past the image, the coefficient base of
 // the image hoisted.
-template <int N, int D, bool Q, bool FAST, bool REAL, bool PARS = false>
+template <int N, int D, bool Q, bool FAST, bool REAL>
 __device__ __forceinline__ float tile_reg_d(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct) {
     constexpr int BPR = TW / N, BPT = (TH / N) * BPR;
@@ -444,43 +423,41 @@ __device__ __forceinline__ float tile_reg_d(const PlanK<N> &P, const FusedGeom &
         const int gy = tc.ty * (TH / N) + by, gx = tc.tx * BPR + bx;
         if (!full && (gy * N >= g.H || gx * N >= g.W)) continue;
         float *coef = zimg ? zimg + (int64_t(gy) * bw + gx) * r : nullptr;
-        sse += block_reg<N, D, Q, FAST, REAL, PARS>(P, tile + by * N * TW + bx * N, r, coef, vec4, recon);
+        sse += block_reg<N, D, Q, FAST, REAL>(P, tile + by * N * TW + bx * N, r, coef, vec4, recon);
     }
     return sse;
 }
 
-template <int N, bool Q, bool FAST, bool REAL, bool PARS = false>
+template <int N, bool Q, bool FAST, bool REAL>
 __device__ __forceinline__ float tile_reg_f(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                             int ct) {
     if constexpr (REAL) {  // one copy for every D it serves (N = 4: all; N = 8: D <= REG_DMAX8)
         return tile_reg_d<N, (N == 4 ? 2 * N - 1 : REG_DMAX8), Q, FAST, true>(P, g, tile, tc, ct);
     } else if constexpr (N == 4) {
         switch (g.D) {
-            case 0: return tile_reg_d<4, 0, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 1: return tile_reg_d<4, 1, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 2: return tile_reg_d<4, 2, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 3: return tile_reg_d<4, 3, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 4: return tile_reg_d<4, 4, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 5: return tile_reg_d<4, 5, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 6: return tile_reg_d<4, 6, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            default: return tile_reg_d<4, 7, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
+            case 0: return tile_reg_d<4, 0, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 1: return tile_reg_d<4, 1, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 2: return tile_reg_d<4, 2, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 3: return tile_reg_d<4, 3, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 4: return tile_reg_d<4, 4, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 5: return tile_reg_d<4, 5, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 6: return tile_reg_d<4, 6, Q, FAST, REAL>(P, g, tile, tc, ct);
+            default: return tile_reg_d<4, 7, Q, FAST, REAL>(P, g, tile, tc, ct);
         }
     } else {
         switch (g.D) {
-            case 0: return tile_reg_d<N, 0, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 1: return tile_reg_d<N, 1, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 2: return tile_reg_d<N, 2, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 3: return tile_reg_d<N, 3, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            case 4: return tile_reg_d<N, 4, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
-            default: return tile_reg_d<N, 5, Q, FAST, REAL, PARS>(P, g, tile, tc, ct);
+            case 0: return tile_reg_d<N, 0, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 1: return tile_reg_d<N, 1, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 2: return tile_reg_d<N, 2, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 3: return tile_reg_d<N, 3, Q, FAST, REAL>(P, g, tile, tc, ct);
+            case 4: return tile_reg_d<N, 4, Q, FAST, REAL>(P, g, tile, tc, ct);
+            default: return tile_reg_d<N, 5, Q, FAST, REAL>(P, g, tile, tc, ct);
         }
     }
 }
 
-// The D dispatch happens once per tile; the benchmark configuration (coefficients
-// and reconstruction, no quantiser) runs a copy with those branches resolved.
-// (Calls without a reconstruction on a plan with T T^T diagonal run the Parseval
-// copy, a kernel of its own: variant REG_PARS.)
+// The D dispatch happens once per tile; calls with coefficients and reconstruction
+// and no quantiser run a copy with those branches resolved (N = 4).
 template <int N, bool Q, bool REAL = false>
 __device__ __forceinline__ float tile_reg(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
                                           int ct) {
@@ -893,7 +870,6 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         constexpr int VB = vbase(V);
         if constexpr (VB == 0) return tile_reg<N, Q>(P, g, tile, tc, ct);
         else if constexpr (VB == REG_REAL) return tile_reg<N, false, true>(P, g, tile, tc, ct);
-        else if constexpr (VB == REG_PARS) return tile_reg_f<N, false, false, false, true>(P, g, tile, tc, ct);
         else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg8_full<Q>(P, g, tile, tc, ct, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
@@ -1090,7 +1066,7 @@ __global__ void __launch_bounds__(ncons(V) + 32, kminb(V))
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    constexpr bool coop = vbase(V) != 0 && vbase(V) != REG_PARS && V != TC_V;
+    constexpr bool coop = vbase(V) != 0 && V != TC_V;
     TcLane tcl;
     uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NC / 32) * TC_ZS);
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
@@ -1222,6 +1198,11 @@ static __global__ void finalize_kernel(const float *partials, int64_t tiles_per_
 // Host launcher (arguments already validated by the C ABI layer).
 template <int N>
 rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) {
+    // rounded plans with T T^T diagonal on the register path: the error by Parseval
+    if constexpr (N == 4 || N == 8) {
+        const rklt_status ps = N == 4 ? launch_pars_n4(plan, a, st) : launch_pars_n8(plan, a, st);
+        if (ps != RKLT_ERR_UNSUPPORTED) return ps;
+    }
     FusedGeom g{};
     g.img = a.img;
     g.recon = a.recon;
@@ -1252,6 +1233,8 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     // scratch: one FP32 SSE partial per tile, stream-ordered from a library pool
     void *scratch = nullptr;
     if (a.partials) {
+        if (g.ntiles * int64_t(sizeof(float)) > a.scratch_cap)
+            return fail(RKLT_ERR_ARG, "scratch array too small for this call");
         g.partials = a.partials;
     } else {
         cudaMemPool_t pool = scratch_pool();
@@ -1270,8 +1253,6 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     // quantised call: the plan's constants plus this call's quantiser tables
     PlanK<N> pq;
     const PlanK<N> *pk = &plan.kparams<N>();
-    // no reconstruction wanted and T T^T diagonal: the register path's Parseval copy
-    if (V == 0 && !a.Q && !a.recon && pk->pm2 != 0) V = REG_PARS;
     if constexpr (N <= 8) {
         if (a.Q) {
             V += QV;
@@ -1301,7 +1282,6 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         switch (V) {
             case 0: fn = reinterpret_cast<const void *>(fused_kernel<4, 0>); break;
             case REG_REAL: fn = reinterpret_cast<const void *>(fused_kernel<4, REG_REAL>); break;
-            case REG_PARS: fn = reinterpret_cast<const void *>(fused_kernel<4, REG_PARS>); break;
             default: fn = reinterpret_cast<const void *>(fused_kernel<4, QV>); break;
         }
     } else if constexpr (N == 8) {
@@ -1310,7 +1290,6 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
             case 1: fn = reinterpret_cast<const void *>(fused_kernel<8, 1>); break;
             case REG_REAL: fn = reinterpret_cast<const void *>(fused_kernel<8, REG_REAL>); break;
             case REG8_FULL: fn = reinterpret_cast<const void *>(fused_kernel<8, REG8_FULL>); break;
-            case REG_PARS: fn = reinterpret_cast<const void *>(fused_kernel<8, REG_PARS>); break;
             case QV: fn = reinterpret_cast<const void *>(fused_kernel<8, QV>); break;
             default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + REG8_FULL>); break;
         }

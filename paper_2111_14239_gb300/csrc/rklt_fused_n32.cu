@@ -6,7 +6,7 @@
 
 namespace rklt {
 rklt_status launch_fused_n32(const Plan &p, const FusedArgs &a, cudaStream_t st) {
-    if (uses_tmem_kernel(p, diag_bound(32, a.r))) return launch_umma32(p, a, st);
+    if (uses_tmem_kernel(p, diag_bound(32, a.r), a.engine)) return launch_umma32(p, a, st);
     return launch_fused<32>(p, a, st);
 }
 unsigned int take_status_n32() { return take_tu_status(); }

@@ -25,8 +25,14 @@ constexpr int kTileH = 64;
 // stored; the kernels' butterflies rebuild the rest.
 template <int N>
 struct PlanK {
+    // Operand pairs of the packed-FP32 register path (N <= 8; one unused entry otherwise):
+    // both lanes of Td[j][l] hold T[j][l], both lanes of Tid[c][j] hold T^{-1}[c][j].
+    static constexpr int RN = N <= 8 ? N : 2;
+    float2 Td[RN][RN / 2];
+    float2 Tid[RN / 2][RN];
     float T[N][N / 2];    // T[i][j], j < N/2           (entries 0, +1, -1)
-    float Ti[N / 2][N];   // T^{-1}[l][j], l < N/2      (inverse of the bare integer T)
+    alignas(8) float Ti[N / 2][N];   // T^{-1}[l][j], l < N/2 (inverse of the bare integer T); pairs
+                                     // (Ti[l][2m], Ti[l][2m+1]) are 8-byte aligned
     float Tih[N / 2][N];  // That^{-1}[l][j] = T^{-1}[l][j] / s_j
     float sij[N][N];      // s_i * s_j (B = sij o C), rounded once from FP64
     float s[N];           // s_i
@@ -66,6 +72,7 @@ struct FusedGeom {
     uint8_t *recon;              // 8-bit reconstruction (may be null)
     float *zcoef;                // compact coefficients (may be null)
     float *partials;             // one FP32 SSE partial per tile
+    unsigned long long *sse_acc; // register path with a Parseval form: per-image error x m^2
     int64_t ld, img_stride;      // source pitch / image stride (bytes)
     int64_t ld_recon, recon_stride;
     int64_t ntiles;              // nimg * tiles_y * tiles_x
@@ -74,7 +81,8 @@ struct FusedGeom {
     int tiles_x, tiles_y;
     int step_img, step_ty, step_tx;  // the grid stride (tiles) in (image, tile row, tile column) form
     int r, D;                    // retained coefficients, diagonal bound
-    int coef_vec4;               // r % 4 == 0 and zcoef 16-byte aligned
+    int coef_vec4;               // r % 4 == 0 and zcoef 16-byte aligned (register path with a
+                                 // Parseval form: widest coefficient store, 4, 2 or 1 floats)
     int use_tma;                 // tiles move by TMA (else plain loads)
     int stages;                  // TMA ring depth
     int inject_stall;            // test hook: the producer issues no loads
@@ -92,7 +100,9 @@ struct FusedArgs {
     int64_t ld_recon, recon_stride;
     double *sse;
     float *psnr;
-    float *partials;   // caller-provided per-tile scratch, or null (library pool)
+    float *partials;   // caller-provided scratch, or null (library pool)
+    int64_t scratch_cap;  // bytes available at partials (when not null)
+    int engine;        // N = 32: tensor engine of this call (0 mma.sync, 1 tcgen05), decided once
     int force_plain;   // 1: plain loads even when TMA would apply
     const double *Q;   // N = 4, 8: JPEG-like quantiser (N*N, host); zcoef then holds int32 Bbar
 };
@@ -101,11 +111,19 @@ rklt_status launch_fused_n4(const Plan &p, const FusedArgs &a, cudaStream_t st);
 rklt_status launch_fused_n8(const Plan &p, const FusedArgs &a, cudaStream_t st);
 rklt_status launch_fused_n16(const Plan &p, const FusedArgs &a, cudaStream_t st);
 rklt_status launch_fused_n32(const Plan &p, const FusedArgs &a, cudaStream_t st);
+// Register path with the error by Parseval's identity (rklt_reg_n{4,8}.cu): serves the
+// call and returns its status, or returns RKLT_ERR_UNSUPPORTED without doing anything
+// when the plan or r is outside its scope.
+rklt_status launch_pars_n4(const Plan &p, const FusedArgs &a, cudaStream_t st);
+rklt_status launch_pars_n8(const Plan &p, const FusedArgs &a, cudaStream_t st);
 unsigned int take_status_n4();
 unsigned int take_status_n8();
 unsigned int take_status_n16();
 unsigned int take_status_n32();
 unsigned int take_status_split();
+unsigned int take_status_reg_n4();
+unsigned int take_status_reg_n8();
+unsigned int take_status_reg_n8b();
 unsigned int take_status_mssim();
 
 // host helpers (rklt_host.cpp)
@@ -130,10 +148,13 @@ int diag_bound(int N, int r);
 // Whether the fused call for (N, D) runs the tensor-memory (tcgen05) kernel, and the
 // rows per tile of the kernel it runs: 32-row strips for that kernel, 64-row tiles
 // otherwise.  The fused call needs one SSE partial per tile.
-inline bool uses_tmem_kernel(const Plan &p, int D) {
-    return p.kind == 0 && p.N == 32 && D <= 16 && tensor_engine() == 1;
+// `engine` is the call's tensor engine (FusedArgs::engine), read once from the
+// library setting when the call enters the C ABI, so that the size check of a
+// caller-provided scratch array and the launch see the same kernel.
+inline bool uses_tmem_kernel(const Plan &p, int D, int engine) {
+    return p.kind == 0 && p.N == 32 && D <= 16 && engine == 1;
 }
-inline int fused_tile_rows(const Plan &p, int D) { return uses_tmem_kernel(p, D) ? 32 : kTileH; }
+inline int fused_tile_rows(const Plan &p, int D, int engine) { return uses_tmem_kernel(p, D, engine) ? 32 : kTileH; }
 
 // Device wait timeout (nanoseconds) for the next launches.
 uint64_t wait_timeout_ns();

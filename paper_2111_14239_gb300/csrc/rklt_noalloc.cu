@@ -1,14 +1,17 @@
 // rklt_noalloc.cu -- rklt_fused without any allocation.
 //
-// rklt_fused takes its per-tile SSE partials (one float per 64 x 256 tile, or per
-// 32 x 256 strip for the N = 32 tensor-memory kernel) from
-// a stream-ordered memory pool.  This variant takes them from a fixed array in
-// the library's own device memory instead, so a call performs no allocation of
-// any kind.  The array is a file-scope __device__ object: every GPU that loads
-// the library holds it (256 KB) until the process exits.  Host code cannot pass
-// the array's name to a kernel -- on the host that name denotes a stand-in
-// object, not device memory -- so its device address is looked up once per
-// device with cudaGetSymbolAddress and cached.
+// rklt_fused takes its scratch (one float per 64 x 256 tile, or per 32 x 256 strip
+// for the N = 32 tensor-memory kernel; one 64-bit accumulator per image on the
+// register path whose error comes from Parseval's identity) from a stream-ordered
+// memory pool.  This variant takes it from a fixed array in the library's own
+// device memory instead, so a call performs no allocation of any kind.  The array
+// is a file-scope __device__ object: every GPU that loads the library holds it
+// (256 KB) until the process exits.  Host code cannot pass the array's name to a
+// kernel -- on the host that name denotes a stand-in object, not device memory --
+// so its device address is looked up with cudaGetSymbolAddress, with the device
+// current, once per device and context.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "rklt_internal.h"
@@ -22,23 +25,55 @@ static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxTiles];
 namespace {
 
 std::mutex g_mu;
-float *g_addr[64] = {};
+struct Cached {
+    unsigned long long ctx = 0;  // context the address belongs to (0: none yet)
+    float *addr = nullptr;
+};
+Cached g_addr[64];
 
-// Device address of g_noalloc_partials on the current device (first call per
-// device performs the lookup).
+// Unique id of the calling thread's current context, or 0 when none is current or
+// the driver entry points are missing.  Ids are never reused, so an address cached
+// under one id cannot outlive the context it came from (a device reset makes a new
+// context with a new id, and the next call looks the address up again).
+unsigned long long current_ctx_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    });
+    if (!get_cur || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    return get_id(c, &id) == CUDA_SUCCESS ? id : 0;
+}
+
+// Device address of g_noalloc_partials on the current device and context (looked
+// up on the first call there).
 rklt_status partials_address(float **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(RKLT_ERR_UNSUPPORTED, "device ordinal above 63");
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_addr[dev].addr || id == 0 || g_addr[dev].ctx != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch array");
-        g_addr[dev] = static_cast<float *>(p);
+        g_addr[dev].addr = static_cast<float *>(p);
+        g_addr[dev].ctx = current_ctx_id();   // the lookup made the device's context current
     }
-    *out = g_addr[dev];
+    *out = g_addr[dev].addr;
     return RKLT_OK;
 }
 
@@ -58,7 +93,9 @@ extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *
     if (ld < W) return fail(RKLT_ERR_SHAPE, "ld must be >= W");
     if (H > 0 && W > 0 && !d_img) return fail(RKLT_ERR_ARG, "d_img is NULL");
     if (d_recon && ld_recon < W) return fail(RKLT_ERR_SHAPE, "ld_recon must be >= W");
-    const int rows = fused_tile_rows(plan->p, diag_bound(N, r));
+    // the kernel is decided here, once: the size check and the launch see the same one
+    const int engine = tensor_engine();
+    const int rows = fused_tile_rows(plan->p, diag_bound(N, r), engine);
     const int64_t tiles = int64_t((H + rows - 1) / rows) * ((W + kTileW - 1) / kTileW);
     if (tiles > kNoAllocMaxTiles)
         return fail(RKLT_ERR_ARG, "image too large for rklt_fused_noalloc: it needs " + std::to_string(tiles) +
@@ -80,7 +117,9 @@ extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *
     a.sse = d_sse;
     a.psnr = d_psnr;
     a.partials = partials;
+    a.scratch_cap = kNoAllocMaxTiles * int64_t(sizeof(float));
     a.force_plain = transport_mode() == 1;
+    a.engine = engine;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (N) {
         case 4: return launch_fused_n4(plan->p, a, s);

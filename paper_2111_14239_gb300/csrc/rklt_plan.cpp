@@ -121,6 +121,12 @@ void fill_kparams(Plan &p) {
             k.Ti[l][j] = float(p.Tinv[size_t(l) * M + j]);
             k.Tih[l][j] = float(p.Tinv[size_t(l) * M + j] / p.s[j]);
         }
+    if constexpr (M <= 8) {
+        for (int j = 0; j < M; j++)
+            for (int l = 0; l < M / 2; l++) k.Td[j][l] = make_float2(k.T[j][l], k.T[j][l]);
+        for (int c = 0; c < M / 2; c++)
+            for (int j = 0; j < M; j++) k.Tid[c][j] = make_float2(k.Ti[c][j], k.Ti[c][j]);
+    }
     for (int i = 0; i < M; i++)
         for (int j = 0; j < M; j++) k.sij[i][j] = float(p.s[i] * p.s[j]);
     for (int i = 0; i < M; i++) k.s[i] = float(p.s[i]);

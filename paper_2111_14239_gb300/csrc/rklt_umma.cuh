@@ -631,6 +631,8 @@ inline rklt_status launch_umma32(const Plan &plan, const FusedArgs &a, cudaStrea
 
     void *scratch = nullptr;
     if (a.partials) {
+        if (g.ntiles * int64_t(sizeof(float)) > a.scratch_cap)
+            return fail(RKLT_ERR_ARG, "scratch array too small for this call");
         g.partials = a.partials;
     } else {
         cudaMemPool_t pool = scratch_pool();

@@ -281,8 +281,8 @@ def zz_diagonals(n, r):
 
 
 def parseval_path(plan, r):
-    """Whether a call without reconstruction takes the integer-Parseval register copy:
-    a rounded plan with T T^T diagonal on the register path (N = 4; N = 8 with D <= 5)."""
+    """Whether a call takes the integer-Parseval register path: a rounded plan with
+    T T^T diagonal on the register path (N = 4; N = 8 with D <= 5)."""
     return plan.kind == 0 and plan.orthogonal and (plan.N == 4 or (plan.N == 8 and zz_diagonals(8, r) <= 5))
 
 
@@ -290,10 +290,10 @@ def parseval_path(plan, r):
 def test_output_subsets_agree(rk, orc, n):
     """Every subset of the optional outputs (coefficients, 8-bit reconstruction) gives
     the same coefficients / reconstruction as the full call, and the same SSE / PSNR
-    bit for bit whenever the reconstruction is formed: the kernels take separate code
-    paths for the full set and the others.  Without a reconstruction, plans with
-    T T^T diagonal take the error from Parseval's identity in integers; that SSE is
-    checked against the oracle and against the full call's."""
+    bit for bit: the kernels take separate code paths for the full set and the
+    others.  Plans with T T^T diagonal on the register path take the error from
+    Parseval's identity in integers with or without a reconstruction (exact integers,
+    so every subset agrees bit for bit); that SSE is also checked against the oracle."""
     H, W = SHAPES[n]
     img = si.ar1_image(H, W, 0.9, 31 + n)
     plan = rk.rklt_make(n, 0.95)
@@ -303,11 +303,9 @@ def test_output_subsets_agree(rk, orc, n):
     for want_coef, want_recon in ((True, False), (False, True), (False, False)):
         zc, rec, sse, ps = run_fused(rk, plan, img, r, pitch=((W + 15) // 16) * 16, want_coef=want_coef,
                                      want_recon=want_recon)
-        if not want_recon and parseval_path(plan, r):
+        if parseval_path(plan, r):
             check_sse(sse, ref, H, W, n)
-            assert abs(sse - full[2]) <= 2 * SSE_REL * ref and abs(ps - full[3]) <= 2e-3
-        else:
-            assert sse == full[2] and ps == full[3]
+        assert sse == full[2] and ps == full[3]
         if want_coef:
             assert np.array_equal(zc, full[0])
         if want_recon:

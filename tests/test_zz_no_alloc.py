@@ -90,3 +90,42 @@ def test_noalloc_rejects_oversized_images(rk):
     st = rk.lib.rklt_fused_noalloc(plan.handle, d, H, W, W, 8, None, None, 0, d, d, None)
     assert st == 1
     assert b"too large" in rk.lib.rklt_last_error()
+
+
+def test_noalloc_rejects_tmem_strips_beyond_the_array(rk):
+    """The N = 32 tensor-memory kernel tiles in 32-row strips: an image that fits the
+    array as 64-row tiles (256 x 256 = 65536) but not as strips (512 x 256) is
+    rejected when that engine is selected.  Host-side check only: the dummy pointers
+    are never dereferenced."""
+    plan = rk.rklt_make(32, 0.95)
+    d = ctypes.c_void_p(256)
+    H, W = 16384, 65536
+    rk.rklt_set_tensor_engine(1)
+    try:
+        st = rk.lib.rklt_fused_noalloc(plan.handle, d, H, W, W, 128, None, None, 0, d, d, None)
+    finally:
+        rk.rklt_set_tensor_engine(0)
+    assert st == 1
+    assert b"too large" in rk.lib.rklt_last_error()
+
+
+def test_noalloc_accepts_exactly_65536_tiles(rk):
+    """The largest accepted image fills the array exactly: 16384 x 65536 pixels in
+    256 x 256 tiles of 64 x 256, N = 16 (one partial per tile).  A zero image has
+    SSE 0 and PSNR +inf; rklt_fused on the same image agrees."""
+    plan = rk.rklt_make(16, 0.95)
+    H, W = 16384, 65536
+    d = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    outs = []
+    for fn in (rk.lib.rklt_fused_noalloc, rk.lib.rklt_fused):
+        sse = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        ps = torch.zeros(1, dtype=torch.float32, device="cuda")
+        st = fn(plan.handle, d.data_ptr(), H, W, W, 32, None, None, 0, sse.data_ptr(), ps.data_ptr(),
+                torch.cuda.current_stream().cuda_stream)
+        assert st == 0, rk.lib.rklt_last_error()
+        torch.cuda.synchronize()
+        outs.append((sse.item(), ps.item()))
+    rk.rklt_device_status()
+    assert outs[0] == outs[1] == (0.0, math.inf)
+    del d
+    torch.cuda.empty_cache()
