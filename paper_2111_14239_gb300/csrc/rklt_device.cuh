@@ -231,6 +231,24 @@ __device__ __forceinline__ uint32_t floor_sat_u8(float x) {
     return u;
 }
 
+// Bytes clip(floor(v0..v3 - 1024), 0, 255) packed little-endian, for v = 1024 + x:
+// binary16 has unit spacing on [1024, 2048), so conversion toward zero is the floor
+// there, and the half 1024 + n has n as its low byte.  The clamp to [1024, 1279] runs
+// on the halves' bit patterns as signed 16-bit integers (negative halves are negative
+// integers, positive ones are ordered like their values), i.e. on the integer ALU,
+// not the floating-point pipe; one permute gathers the four low bytes.
+__device__ __forceinline__ uint32_t bytes4_biased(float v0, float v1, float v2, float v3) {
+    uint32_t h01, h23;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h01) : "f"(v1), "f"(v0));
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h23) : "f"(v3), "f"(v2));
+    const uint32_t lo = 0x64006400u, hi = 0x64FF64FFu;
+    asm("max.s16x2 %0, %0, %1;" : "+r"(h01) : "r"(lo));
+    asm("min.s16x2 %0, %0, %1;" : "+r"(h01) : "r"(hi));
+    asm("max.s16x2 %0, %0, %1;" : "+r"(h23) : "r"(lo));
+    asm("min.s16x2 %0, %0, %1;" : "+r"(h23) : "r"(hi));
+    return __byte_perm(h01, h23, 0x6420);
+}
+
 // clip(floor(x + 1/2), 0, 255): round-half-up then saturate to 8 bits.
 __device__ __forceinline__ uint32_t recon_byte(float x) {
     float v = fminf(fmaxf(x + 0.5f, 0.0f), 255.0f);

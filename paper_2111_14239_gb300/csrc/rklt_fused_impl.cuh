@@ -53,7 +53,8 @@ constexpr int TH = 64;           // tile height in rows
 constexpr int TILE_BYTES = TW * TH;
 constexpr int STAGES = 8;        // deepest TMA ring (barrier and reduction slots)
 constexpr int NCONS = 256;       // consumer threads (8 warps) of the FMA variants; one producer warp follows
-constexpr int NCONS_TC = 256;    // consumer threads (8 warps) of the tensor-core variant
+constexpr int NCONS_TC = 128;    // consumer threads (4 warps) of the tensor-core variant: three CTAs of
+                                 // 4 + 1 warps per SM leave each thread up to 128 registers
 constexpr int NCONS_MAX = 256;
 constexpr int LDY = TW + 1;      // padded row stride of the cooperative exchange buffer (floats)
 static_assert(TW == kTileW && TH == kTileH, "tile geometry is declared in rklt_internal.h");
@@ -860,7 +861,7 @@ __host__ __device__ inline int real_variant(int N, int D) {
 
 // Consumer threads of kernel variant V, and the CTAs per SM its registers are sized for.
 __host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : NCONS; }
-__host__ __device__ constexpr int kminb(int V) { return vbase(V) == REG8_FULL ? 1 : 2; }
+__host__ __device__ constexpr int kminb(int V) { return vbase(V) == REG8_FULL ? 1 : (V == TC_V ? 3 : 2); }
 
 template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
@@ -1275,7 +1276,7 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
         if (tma && !a.recon) tout = tin;
     }
     g.use_tma = tma ? 1 : 0;
-    g.stages = swz ? 6 : (N >= 16 ? 3 : 4);
+    g.stages = swz ? 3 : (N >= 16 ? 3 : 4);
     const SmemLayout L = smem_layout<N>(tma ? g.stages : 1, a.r, g.D, vbase(V));
     const void *fn = nullptr;
     if constexpr (N == 4) {

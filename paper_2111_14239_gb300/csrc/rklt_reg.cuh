@@ -33,24 +33,6 @@ namespace rklt {
 
 constexpr int PARS_DMAX8 = 5;   // N = 8: diagonal bounds served here (r <= 15)
 
-// Bytes clip(floor(v0..v3 - 1024), 0, 255) packed little-endian, for v = 1024 + x:
-// binary16 has unit spacing on [1024, 2048), so conversion toward zero is the floor
-// there, and the half 1024 + n has n as its low byte.  The clamp to [1024, 1279] runs
-// on the halves' bit patterns as signed 16-bit integers (negative halves are negative
-// integers, positive ones are ordered like their values), i.e. on the integer ALU,
-// not the floating-point pipe; one permute gathers the four low bytes.
-__device__ __forceinline__ uint32_t bytes4_biased(float v0, float v1, float v2, float v3) {
-    uint32_t h01, h23;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h01) : "f"(v1), "f"(v0));
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h23) : "f"(v3), "f"(v2));
-    const uint32_t lo = 0x64006400u, hi = 0x64FF64FFu;
-    asm("max.s16x2 %0, %0, %1;" : "+r"(h01) : "r"(lo));
-    asm("min.s16x2 %0, %0, %1;" : "+r"(h01) : "r"(hi));
-    asm("max.s16x2 %0, %0, %1;" : "+r"(h23) : "r"(lo));
-    asm("min.s16x2 %0, %0, %1;" : "+r"(h23) : "r"(hi));
-    return __byte_perm(h01, h23, 0x6420);
-}
-
 __device__ __forceinline__ float2 ld_pair(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
 // B blocks held in registers (w[b], N/4 words per row), transformed together: every

@@ -320,8 +320,11 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     //      31 - x' (E' - O'), then error and 8-bit output for the m-tile's two rows.
     //      Row q of the lane: m-tile q >> 1, accumulator row half q & 1; top word
     //      x' = 4t .. 4t+3, bottom word x' = 28-4t .. 31-4t.
-    const __half2 k10235 = __float2half2_rn(1023.5f);
-    const float half4[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+    // the even sums start at 1024 + 1/2: E + O and E - O are A' + 1024 + 1/2, whose
+    // binary16 truncation is the rounded byte biased by 1024 (bytes4_biased), and whose
+    // difference from the biased pixel 1024 + a is the error less 1/2
+    const float k10245[4] = {1024.5f, 1024.5f, 1024.5f, 1024.5f};
+    const float2 half2f = make_float2(0.5f, 0.5f);
     float2 sse2 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int mt = 0; mt < 2; mt++) {
@@ -334,7 +337,7 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
         for (int nt = 0; nt < 2; nt++) {
             const uint4 b4 = lds128(tabl + (2 + nt) * 512);
             const uint32_t l4e = lds32(tabl + (13 + nt) * 512 + 8), l4o = lds32(tabl + (13 + nt) * 512 + 12);
-            mma16(E2[nt], half4, ah0, ah1, al0, al1, b4.x, b4.y);
+            mma16(E2[nt], k10245, ah0, ah1, al0, al1, b4.x, b4.y);
             mma8(E2[nt], ah0, ah1, l4e);
             mma16(O2[nt], z4, oh0, oh1, ol0, ol1, b4.z, b4.w);
             mma8(O2[nt], oh0, oh1, l4o);
@@ -349,23 +352,21 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
             const float2 ta = __fadd2_rn(e0, o0), tb = __fadd2_rn(e1, o1);              // x' = 4t + {0,1}, {2,3}
             const float2 ba = __ffma2_rn(o0, neg1, e0), bb = __ffma2_rn(o1, neg1, e1);  // bytes {3,2}, {1,0}
             const uint32_t wt = ld_word(q, 0), wb = ld_word(q, 2);
-            const __half2 p01 = __hsub2(as_h2(bytes_to_biased_h2(wt, 0, 1)), k10235);   // pixel + 1/2
-            const __half2 p23 = __hsub2(as_h2(bytes_to_biased_h2(wt, 2, 3)), k10235);
-            const __half2 q01 = __hsub2(as_h2(bytes_to_biased_h2(wb, 0, 1)), k10235);
-            const __half2 q23 = __hsub2(as_h2(bytes_to_biased_h2(wb, 2, 3)), k10235);
-            const float2 et0 = make_float2(sub_h_f(__low2half(p01), ta.x), sub_h_f(__high2half(p01), ta.y));
-            const float2 et1 = make_float2(sub_h_f(__low2half(p23), tb.x), sub_h_f(__high2half(p23), tb.y));
-            const float2 eb0 = make_float2(sub_h_f(__low2half(q01), bb.y), sub_h_f(__high2half(q01), bb.x));
-            const float2 eb1 = make_float2(sub_h_f(__low2half(q23), ba.y), sub_h_f(__high2half(q23), ba.x));
+            const __half2 p01 = as_h2(bytes_to_biased_h2(wt, 0, 1));   // 1024 + pixel
+            const __half2 p23 = as_h2(bytes_to_biased_h2(wt, 2, 3));
+            const __half2 q01 = as_h2(bytes_to_biased_h2(wb, 0, 1));
+            const __half2 q23 = as_h2(bytes_to_biased_h2(wb, 2, 3));
+            const float2 et0 = __fadd2_rn(make_float2(sub_h_f(__low2half(p01), ta.x), sub_h_f(__high2half(p01), ta.y)), half2f);
+            const float2 et1 = __fadd2_rn(make_float2(sub_h_f(__low2half(p23), tb.x), sub_h_f(__high2half(p23), tb.y)), half2f);
+            const float2 eb0 = __fadd2_rn(make_float2(sub_h_f(__low2half(q01), bb.y), sub_h_f(__high2half(q01), bb.x)), half2f);
+            const float2 eb1 = __fadd2_rn(make_float2(sub_h_f(__low2half(q23), ba.y), sub_h_f(__high2half(q23), ba.x)), half2f);
             sse2 = __ffma2_rn(et0, et0, sse2);
             sse2 = __ffma2_rn(et1, et1, sse2);
             sse2 = __ffma2_rn(eb0, eb0, sse2);
             sse2 = __ffma2_rn(eb1, eb1, sse2);
             if (recon) {
-                st_word(q, 0, __byte_perm(__byte_perm(floor_sat_u8(ta.x), floor_sat_u8(ta.y), 0x0040),
-                                          __byte_perm(floor_sat_u8(tb.x), floor_sat_u8(tb.y), 0x0040), 0x5410));
-                st_word(q, 2, __byte_perm(__byte_perm(floor_sat_u8(bb.y), floor_sat_u8(bb.x), 0x0040),
-                                          __byte_perm(floor_sat_u8(ba.y), floor_sat_u8(ba.x), 0x0040), 0x5410));
+                st_word(q, 0, bytes4_biased(ta.x, ta.y, tb.x, tb.y));
+                st_word(q, 2, bytes4_biased(bb.y, bb.x, ba.y, ba.x));
             }
         }
     }
@@ -388,22 +389,28 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     return sse2.x + sse2.y;
 }
 
-// The 16 blocks of one tile: warp w takes block column w of both block rows.
+// The 16 blocks of one tile: warp w takes block columns w and w + 4 of both block
+// rows.  Column w + 4 lies in the second 128-byte half of the tile at the same
+// swizzle phase, so its addresses are column w's plus TC_HALF.
 template <bool FAST>
 __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                          const TileCoord &tc, int ct, uint32_t zs) {
-    const int bx = ct >> 5, lane = ct & 31;
+    const int w = ct >> 5, lane = ct & 31;
     const int bw = g.W / 32;
     const int rows_in = min(TH / 32, (g.H - tc.ty * TH) / 32);
     const int nb_in = min(TW / 32, bw - tc.tx * (TW / 32));
     float sse = 0.0f;
-    if (bx >= nb_in) return sse;
-    for (int by = 0; by < rows_in; by++) {
-        float *zg = (FAST || g.zcoef) ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img +
-                                                   int64_t(tc.ty * (TH / 32) + by) * bw + tc.tx * (TW / 32) + bx) * g.r
-                                      : nullptr;
-        sse += tc_block32<FAST>(c, tabl, smem_u32(tile) + by * 32 * 128, lane, g.r, zg, zs, g.recon != nullptr,
-                                g.coef_vec4 != 0);
+    float *zt = (FAST || g.zcoef) ? g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * (TH / 32)) * bw +
+                                               tc.tx * (TW / 32) + w) * g.r
+                                  : nullptr;
+#pragma unroll 1
+    for (int cg = 0; cg < 2; cg++) {
+        if (w + 4 * cg >= nb_in) break;
+        for (int by = 0; by < rows_in; by++) {
+            float *zg = zt ? zt + (int64_t(by) * bw + 4 * cg) * g.r : nullptr;
+            sse += tc_block32<FAST>(c, tabl, smem_u32(tile) + by * 32 * 128 + cg * TC_HALF, lane, g.r, zg, zs,
+                                    g.recon != nullptr, g.coef_vec4 != 0);
+        }
     }
     return sse;
 }
@@ -614,8 +621,9 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     //      rows g (group 2 mt) and g + 8 (group 2 mt + 1): y = g, 16 + g (mt 0) and
     //      15 - g, 31 - g (mt 1); lane word x = 16 hb + 4t .. 4t + 3
     const uint4 b4 = lds128(tabl + 7 * 512), b4l = lds128(tabl + 8 * 512);
-    const __half2 k10235 = __float2half2_rn(1023.5f);
-    const float half4[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+    // accumulators start at 1024 + 1/2 (see tc_block32)
+    const float k10245[4] = {1024.5f, 1024.5f, 1024.5f, 1024.5f};
+    const float2 half2f = make_float2(0.5f, 0.5f);
     float2 sse2 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int mt = 0; mt < 2; mt++) {
@@ -624,9 +632,9 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
             const uint32_t ah0 = movm_t(yh[2 * mt][hb]), ah1 = movm_t(yh[2 * mt + 1][hb]);
             const uint32_t al0 = movm_t(yl[2 * mt][hb]), al1 = movm_t(yl[2 * mt + 1][hb]);
             float R[2][4];
-            mma16(R[0], half4, ah0, ah1, al0, al1, b4.x, b4.y);
+            mma16(R[0], k10245, ah0, ah1, al0, al1, b4.x, b4.y);
             mma8(R[0], ah0, ah1, b4l.x);
-            mma16(R[1], half4, ah0, ah1, al0, al1, b4.z, b4.w);
+            mma16(R[1], k10245, ah0, ah1, al0, al1, b4.z, b4.w);
             mma8(R[1], ah0, ah1, b4l.y);
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -637,16 +645,14 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
                 const int lq = (q == 0) ? 0 : (q == 1) ? 1 : (q == 2) ? 2 : 3;
                 // lane rows: ld_word's q follows y = g, 16 + g, 15 - g, 31 - g
                 const uint32_t wt = ld_word(lq, hb);
-                const __half2 p01 = __hsub2(as_h2(bytes_to_biased_h2(wt, 0, 1)), k10235);
-                const __half2 p23 = __hsub2(as_h2(bytes_to_biased_h2(wt, 2, 3)), k10235);
-                float2 e0 = make_float2(sub_h_f(__low2half(p01), va.x), sub_h_f(__high2half(p01), va.y));
-                float2 e1 = make_float2(sub_h_f(__low2half(p23), vc.x), sub_h_f(__high2half(p23), vc.y));
+                const __half2 p01 = as_h2(bytes_to_biased_h2(wt, 0, 1));   // 1024 + pixel
+                const __half2 p23 = as_h2(bytes_to_biased_h2(wt, 2, 3));
+                float2 e0 = __fadd2_rn(make_float2(sub_h_f(__low2half(p01), va.x), sub_h_f(__high2half(p01), va.y)), half2f);
+                float2 e1 = __fadd2_rn(make_float2(sub_h_f(__low2half(p23), vc.x), sub_h_f(__high2half(p23), vc.y)), half2f);
                 if (!ALL_IN && !((in >> (2 * vb + hb)) & 1)) e0 = e1 = make_float2(0.0f, 0.0f);
                 sse2 = __ffma2_rn(e0, e0, sse2);
                 sse2 = __ffma2_rn(e1, e1, sse2);
-                if (recon)
-                    st_word(lq, hb, __byte_perm(__byte_perm(floor_sat_u8(va.x), floor_sat_u8(va.y), 0x0040),
-                                                __byte_perm(floor_sat_u8(vc.x), floor_sat_u8(vc.y), 0x0040), 0x5410));
+                if (recon) st_word(lq, hb, bytes4_biased(va.x, va.y, vc.x, vc.y));
             }
         }
     }
@@ -654,19 +660,23 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     return sse2.x + sse2.y;
 }
 
-// The 16 regions of one tile (N = 16): warp w takes region column w of both region rows.
+// The 16 regions of one tile (N = 16): warp w takes region columns w and w + 4 (the
+// latter TC_HALF further in the swizzled tile) of both region rows.
 template <bool FAST>
 __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                            const TileCoord &tc, int ct, uint32_t zs) {
-    const int lane = ct & 31, w = ct >> 5;
+    const int lane = ct & 31;
     const int bw = g.W / 16;
     const int rows_in = min(TH / 16, (g.H - tc.ty * TH) / 16);   // block rows of the tile inside
     const int nb_in = min(TW / 16, bw - tc.tx * (TW / 16));       // block columns inside
-    const uint32_t t32 = smem_u32(tile);
     const int r = g.r;
     float sse = 0.0f;
-    if (2 * w >= nb_in) return sse;
     const bool coef = FAST || g.zcoef != nullptr;
+#pragma unroll 1
+    for (int cg = 0; cg < 2; cg++) {
+    const int w = (ct >> 5) + 4 * cg;
+    const uint32_t t32 = smem_u32(tile) + cg * TC_HALF;
+    if (2 * w >= nb_in) break;
     const bool cols2 = 2 * w + 1 < nb_in;   // both block columns of the warp inside
     for (int ry = 0; ry < 2; ry++) {
         if (2 * ry >= rows_in) break;
@@ -696,6 +706,7 @@ __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const
             }
             __syncwarp();
         }
+    }
     }
     return sse;
 }
