@@ -67,12 +67,13 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.skip = 0
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix=f"rklt_clocks_gpu{self.gpu}_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -97,6 +98,15 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        s = self._summary()
+        try:
+            if self.path:
+                os.unlink(self.path)
+        except OSError:
+            pass
+        return s
+
+    def _summary(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm, smax, reasons = [], None, set()
@@ -121,10 +131,10 @@ class ClockSampler:
 
 
 def make_images(rank: int = 0):
-    """This rank's 16 images: seeds 2000 + 16*rank + i (rank 0 = the single-GPU workload)."""
+    """This rank's 16 images: seeds 2000 + 16*rank + i (rank 0 = the single-GPU workload).
+    Imports only the input generators, so the oracle arm never loads the CUDA library."""
     import synth_inputs as si
-    from paper_2111_14239_gb300 import replicas
-    return si.roofline_batch(NIMG, SIDE, replicas.image_seeds(2000, NIMG, rank)[0])
+    return si.roofline_batch(NIMG, SIDE, si.rank_seeds(2000, NIMG, rank)[0])
 
 
 # ---------------------------------------------------------------------------
@@ -217,7 +227,7 @@ def run_ours(args):
             ps=torch.empty(NIMG, dtype=torch.float32, device=dev))
     stream = torch.cuda.current_stream(dev)
 
-    def step(ev=None):
+    def one_pass(ev=None):
         for n in NS:
             o = outs[n]
             if ev is not None:
@@ -226,6 +236,29 @@ def run_ours(args):
                                   stream=stream)
             if ev is not None:
                 ev[n][1].record(stream)
+
+    # one step = `passes` passes over the 16 images, chosen so that the K timed steps
+    # last at least --min-timed-s on the device (steadier kernel times, several clock
+    # samples); the per-kernel events bracket the first pass of every step
+    for _ in range(3):
+        one_pass()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    pass_ms = e0.elapsed_time(e1) / 5
+    passes = max(1, math.ceil(args.min_timed_s * 1e3 / (args.steps * pass_ms)))
+    if dist:  # every rank runs the same number of passes
+        t = torch.tensor([passes], dtype=torch.int64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        passes = int(t.item())
+
+    def step(ev=None):
+        for p in range(passes):
+            one_pass(ev if p == 0 else None)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -253,7 +286,7 @@ def run_ours(args):
     ms = replicas.max_over_ranks(ms, dev)
     rk.rklt_device_status()
 
-    px_step = len(NS) * NIMG * H * W
+    px_step = len(NS) * NIMG * H * W * passes
     value = replicas.job_throughput(px_step * args.steps, world, ms / 1e3) / 1e6
 
     # ---- end to end through the C ABI with host buffers
@@ -302,7 +335,8 @@ def run_ours(args):
     e2e_ms = replicas.max_over_ranks(s2.elapsed_time(t2), dev)
     h2d = imgs_np.nbytes
     d2h = sum(pin_out[n]["zc"].numel() * 4 + pin_out[n]["rec"].numel() + NIMG * 4 for n in NS)
-    e2e_val = px_step * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
+    px_pass = len(NS) * NIMG * H * W
+    e2e_val = px_pass * e2e_steps * world / (e2e_ms / 1e3) / 1e6 if e2e_steps else None
 
     psnr = {n: [round(float(x), 4) for x in outs[n]["ps"].cpu().tolist()[:2]] for n in NS}
 
@@ -349,19 +383,26 @@ def run_ours(args):
     line = {
         "metric": "Mpixel/s fwd+zonal+inv+PSNR",
         "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8 in / int-exact f32 T-stage / f32 inverse", "data": "synthetic AR(1) uint8 (seeded)",
+        "ms_per_step": ms / args.steps, "ms_per_pass": ms / (args.steps * passes),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": ("u8 in / int-exact T-stage / f32 inverse (N = 16, 32: tensor-core inverse on two binary16 "
+                  "digits per operand, about 22 significant bits, f32 accumulation)"),
+        "data": "synthetic AR(1) uint8 (seeded)",
         "config": {"workload": "roofline_4096: 16 x 4096x4096 AR(1) rho=0.95, N in {4,8,16,32}, r=N^2/8, "
                                "outputs: compact coeffs + uint8 recon + PSNR",
                    "images_per_gpu": NIMG, "side": SIDE, "block_sizes": list(NS), "r": [rs[n] for n in NS],
-                   "l2": "inputs 268 MB > 129 MB L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+                   "l2": "inputs 268 MB > 129 MB L2 (no flush needed)", "parallelism": f"replicas x{world}",
+                   "passes_per_step": passes, "timed_ms": round(ms, 2),
+                   "step": "passes_per_step passes of the fused call over the 16 images for every N"},
         "roofline": {"bound": "hbm", "achieved": dk["GB/s"], "peak": hbm, "unit": "GB/s",
                      "frac": round(dk["GB/s"] / hbm, 4), "traffic": traffic,
                      "kernel": dk["kernel"], "peak_source": f"{hbm_src} hbm_gbs (MEASURED_PEAKS.json)"},
         "per_block_size": per_n,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * len(NS) * args.steps,
+        # per pass and N: the fused kernel and the per-image finalize kernel (plus a
+        # memset of the error accumulators on the register path)
+        "gpu_launches": 2 * len(NS) * args.steps * passes,
         "clocks": clk.summary(),
         "psnr_sample_db": psnr,
         "workloads": workloads,
@@ -432,10 +473,24 @@ def leg_psnr_only(rk, d_img, dev, stream):
         gbs = nimg * H * W * 1.0 / (ms / 1e3) / 1e9
         # N <= 8 with T T^T diagonal: the error by Parseval in integers, no inverse
         pars = plan.kind == 0 and plan.orthogonal and (n == 4 or (n == 8 and n * n // 8 <= 15))
+        kern = (f"pars_kernel<{n}, {zz_bound(n, n * n // 8)}, 0>" if pars else
+                f"fused_kernel<{n}, 4>")
         out[str(n)] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
                        "psnr_db_img0": round(float(ps[0].item()), 4),
-                       "error_by": "parseval (integers)" if pars else "inverse transform"}
+                       "error_by": "parseval (integers)" if pars else "inverse transform",
+                       "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                                    "frac": round(gbs / hbm, 4), "traffic": None, "kernel": kern,
+                                    "bytes_per_px": 1.0}}
     return out
+
+
+def zz_bound(n, r):
+    """Diagonal bound D of the first r zig-zag positions (every kept (i, j) has i + j < D)."""
+    d, cnt = 0, 0
+    while cnt < r:
+        cnt += min(d, 2 * n - 2 - d) + 1
+        d += 1
+    return d
 
 
 def leg_comparison(rk, d_img, dev, stream):
@@ -489,10 +544,19 @@ def leg_quant(rk, d_img, dev, stream):
             "bytes_per_px": bytes_px, "psnr_db_img0": round(float(ps[0].item()), 4)}
 
 
-def fp32_peak_tflops(sm_mhz=2070.0):
-    """FP32 FMA peak from the unit counts and the maximum SM clock (GB300: 152 SMs x
-    128 lanes)."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(dev, sm_mhz=None):
+    """FP32 FMA peak from the unit counts and the maximum SM clock: the device's SM
+    count (cudaGetDeviceProperties) x 128 FP32 lanes x 2 flop x clock (default: the
+    maximum SM clock recorded in MEASURED_PEAKS.json, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if sm_mhz is None:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                sm_mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            sm_mhz = 2070.0
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms, sm_mhz
 
 
 def leg_mssim(rk, d_img, dev, stream):
@@ -515,12 +579,13 @@ def leg_mssim(rk, d_img, dev, stream):
     # FP32 flop per output position; peak = 152 SMs x 128 FP32 lanes x 2 flop x SM clock
     npos = nimg * (H - 10) * (W - 10)
     tflops = npos * 176.0 / (ms / 1e3) / 1e12
-    fp32_peak = fp32_peak_tflops()
+    fp32_peak, sms, mhz = fp32_peak_tflops(dev)
     return {"workload": f"{nimg} x {H}x{W}: original vs 8-bit RKLT reconstruction (N=8, r=8)",
             "ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
             "roofline": {"bound": "alu", "achieved": round(tflops, 2), "peak": round(fp32_peak, 1),
                          "unit": "TFLOP/s", "frac": round(tflops / fp32_peak, 4),
-                         "flop_per_position": 176, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                         "flop_per_position": 176,
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (device properties)"},
             "mssim_img0": round(float(out[0].item()), 6), "psnr_db_img0": round(float(ps[0].item()), 4)}
 
 
@@ -579,16 +644,24 @@ def leg_batch(rk, dev, stream, n_images=2000):
     px = sum(it.h * it.w for it in items)
     info = batch.info()
     batch.close()
+    # algorithmic bytes: per image 1 B read + 4 r / 64 B coefficients + 1 B reconstruction per pixel
+    alg = sum(it.h * it.w * (2.0 + 4.0 * it.r / 64.0) for it in items)
+    hbm, _ = peaks()
+    gbs = alg / (ms_batch / 1e3) / 1e9
     return {"workload": f"{n_images} AR(1) crops, sides U{{64..4096/8}}, N=8, r~U{{1..64}}, nearest of 10 RKLTs",
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(gbs / hbm, 4), "traffic": None, "alg_bytes": alg},
             "gpixel": px / 1e9, "graph_batch_ms": ms_batch, "plain_launches_ms": ms_plain,
             "graph_batch_mpixel_per_s": px / (ms_batch / 1e3) / 1e6,
             "plain_mpixel_per_s": px / (ms_plain / 1e3) / 1e6, "speedup": ms_plain / ms_batch,
             "max_rel_sse_diff_vs_plain": rel, "autotuned": info}
 
 
-def leg_serve(rk, dev, duration_s=6.0, rate=2000.0):
-    """Poisson 2000 req/s; lognormal sides (median 768, sigma 0.5); rho in
-    {0.5, 0.8, 0.9, 0.95}; r ~ U{1..64}; 8 GB budget: continuous batching vs plain."""
+def leg_serve(rk, dev, duration_s=60.0, rate=2000.0, stress_s=10.0):
+    """Config 5: Poisson 2000 req/s for 60 s (about 120 000 requests); lognormal sides
+    (median 768, sigma 0.5); rho in {0.5, 0.8, 0.9, 0.95}; r ~ U{1..64}; 8 GB budget.
+    The library's native request loop, continuous batching against one request at
+    a time (the latter run twice on the same trace); then a 4x stress rate."""
     import synth_inputs as si
     from paper_2111_14239_gb300 import serve
     rhos = (0.5, 0.8, 0.9, 0.95)
@@ -597,11 +670,15 @@ def leg_serve(rk, dev, duration_s=6.0, rate=2000.0):
     srv = serve.Server(rhos, budget_bytes=8 << 30, streams=4)
     out = {"workload": f"Poisson arrivals, lognormal sides (median 768, sigma 0.5), N=8, "
                        f"rho in {{0.5,0.8,0.9,0.95}}, r~U{{1..64}}, 8 GB budget; nominal {rate:.0f} req/s "
-                       f"for {duration_s:.0f} s and a 4x stress rate for {duration_s / 2:.0f} s"}
-    for tag, rr, dur in (("nominal", rate, duration_s), ("stress_4x", 4 * rate, duration_s / 2)):
+                       f"for {duration_s:.0f} s and a 4x stress rate for {stress_s:.0f} s; native request loop",
+           "latency": "arrival to results (reconstruction, coefficients, SSE, PSNR) in pinned host memory"}
+    for tag, rr, dur, plain_runs in (("nominal", rate, duration_s, 2), ("stress_4x", 4 * rate, stress_s, 1)):
         cont = srv.run(serve.make_trace(rr, dur, pool, seed=5000, rhos=rhos))
-        plain = serve.serve_plain(srv.plans, serve.make_trace(rr, dur, pool, seed=5000, rhos=rhos))
-        out[tag] = {"rate_req_per_s": rr, "continuous_batching": cont, "plain_per_request": plain}
+        plains = [srv.run(serve.make_trace(rr, dur, pool, seed=5000, rhos=rhos), mode=serve.PLAIN)
+                  for _ in range(plain_runs)]
+        out[tag] = {"rate_req_per_s": rr, "continuous_batching": cont,
+                    "plain_per_request": plains[0] if plain_runs == 1 else plains}
+    srv.close()
     return out
 
 def main():
@@ -615,7 +692,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--block-sizes", default="4,8,16,32", help="subset of N (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the single/sweep/batch/serving legs")
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--min-timed-s", type=float, default=1.0,
+                    help="lower bound on the device-timed region (passes per step scale to reach it)")
     ap.add_argument("--legs", default="", help="comma-separated subset of the extra legs (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -277,6 +277,67 @@ rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm,
 /* Wait for the batch's own stream, free its device memory and graph (NULL ignored). */
 void rklt_batch_destroy(rklt_batch *b);
 
+/* Request loop (serving).  A server owns one device buffer of budget_bytes (the
+ * device-memory budget requests are admitted against), a pinned host mirror of
+ * it, nstreams CUDA streams and result slots for batches of up to max_batch
+ * requests; plans (rounded plans, all of one N: 4 or 8) stay host-side and travel
+ * with each launch.  Creation allocates all of that and runs every kernel both
+ * loops can reach once on a small image (so no request pays for module loading);
+ * it synchronises the device.  Release with rklt_server_destroy.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_UNSUPPORTED (N), RKLT_ERR_OOM, RKLT_ERR_CUDA. */
+typedef struct rklt_server rklt_server;
+
+/* One request: compress + decompress + PSNR (Sec. 4.1 per image) of the H x W
+ * uint8 image at h_img (host memory, pitch W, read when the request is admitted)
+ * with plans[plan] and r retained coefficients; it arrives arrival_s seconds after
+ * the start of the run.  Arrivals must be non-decreasing. */
+typedef struct rklt_request {
+    double arrival_s;
+    const uint8_t *h_img;
+    int H, W;
+    int plan;
+    int r;
+} rklt_request;
+
+/* Outcome of one request: the time its launch was issued (admit_s) and its
+ * completion time (done_s), both in seconds from the start of the run (the clock
+ * of arrival_s); SSE and PSNR (as rklt_fused); status RKLT_OK or RKLT_ERR_BUDGET
+ * (the request alone needs more than the budget; rejected). */
+typedef struct rklt_result {
+    double done_s;
+    double admit_s;
+    double sse;
+    float psnr;
+    int status;
+} rklt_result;
+
+rklt_status rklt_server_create(const rklt_plan *const *plans, int nplans, size_t budget_bytes, int nstreams,
+                               int max_batch, rklt_server **out);
+
+/* Replay n requests in real time on the calling thread and fill results[0..n).
+ * mode 0 = continuous batching: a waiting request is admitted (first come, first
+ * served) as soon as its input, 8-bit reconstruction and coefficients fit in a
+ * first-fit arena over the budget; every request admitted in one pass of the loop
+ * goes out in one rklt_fused_items launch on the next stream, so batches overlap
+ * on the device; a request completes when its batch's copies back to pinned
+ * memory have finished.  mode 1 = one request at a time: copy in, rklt_fused,
+ * copy out, synchronise.  h_recon[i] (H x W bytes) and h_coef[i] ([blocks][r]
+ * FP32) receive request i's outputs when the arrays and entries are non-NULL.
+ * *wall_s = duration of the run.  Calls on one server must not overlap.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_BUDGET (mode 1: a request exceeds
+ * the budget), RKLT_ERR_CUDA. */
+rklt_status rklt_server_run(rklt_server *s, const rklt_request *reqs, int n, int mode, uint8_t *const *h_recon,
+                            float *const *h_coef, rklt_result *results, double *wall_s);
+
+/* Wait for the server's streams and free everything it owns (NULL ignored). */
+void rklt_server_destroy(rklt_server *s);
+
+/* Host-only check of the server's first-fit arena (no GPU needed): `steps` random
+ * allocations and releases over a 64 KB arena; fails (RKLT_ERR_ARG, message in
+ * rklt_last_error) if two live ranges overlap, a range is misaligned, or releasing
+ * everything does not coalesce the free list back into one range. */
+rklt_status rklt_arena_selftest(unsigned seed, int steps);
+
 /* r-sweep: for nimg same-shape images and nplans plans (all with the same N, 4 or
  * 8), the SSE and PSNR of the reconstruction that keeps the first r zig-zag
  * coefficients, for every r = 1..N*N (Sec. 4.1 zonal retention swept over r, as

@@ -23,6 +23,7 @@ __all__ = [
     "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_mssim", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
+    "RklTRequest", "RklTResult", "NativeServer", "rklt_server_create",
 ]
 
 STATUS = {0: "RKLT_OK", 1: "RKLT_ERR_ARG", 2: "RKLT_ERR_SHAPE", 3: "RKLT_ERR_DEGENERATE", 4: "RKLT_ERR_CUDA",
@@ -37,6 +38,18 @@ class RklTItem(ctypes.Structure):
     _fields_ = [("d_img", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("ld", ctypes.c_int64),
                 ("plan", ctypes.c_int), ("r", ctypes.c_int), ("d_zcoef", ctypes.c_void_p),
                 ("d_recon", ctypes.c_void_p), ("ld_recon", ctypes.c_int64)]
+
+
+class RklTRequest(ctypes.Structure):
+    """rklt_request of include/rklt.h."""
+    _fields_ = [("arrival_s", ctypes.c_double), ("h_img", ctypes.c_void_p), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("plan", ctypes.c_int), ("r", ctypes.c_int)]
+
+
+class RklTResult(ctypes.Structure):
+    """rklt_result of include/rklt.h."""
+    _fields_ = [("done_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("sse", ctypes.c_double),
+                ("psnr", ctypes.c_float), ("status", ctypes.c_int)]
 
 
 class RklTError(RuntimeError):
@@ -85,6 +98,10 @@ _SIGS = {
     "rklt_batch_info": (_I, [_P, _P, _P, _P, _P]),
     "rklt_batch_destroy": (None, [_P]),
     "rklt_rsweep": (_I, [_P, _I, _P, _I, _I, _I, _L, _L, _P, _P, _P]),
+    "rklt_server_create": (_I, [_P, _I, ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
+    "rklt_server_run": (_I, [_P, _P, _I, _I, _P, _P, _P, ctypes.POINTER(_D)]),
+    "rklt_server_destroy": (None, [_P]),
+    "rklt_arena_selftest": (_I, [ctypes.c_uint, _I]),
     "rklt_set_wait_timeout_us": (None, [_U32]),
     "rklt_set_transport": (None, [_I]),
     "rklt_set_tensor_engine": (None, [_I]),
@@ -426,3 +443,49 @@ def rklt_debug_inject_stall(on: bool):
 
 def rklt_version() -> int:
     return lib.rklt_version()
+
+
+class NativeServer:
+    """rklt_server: the library's request loop (continuous batching, or one request at
+    a time) over a device-memory budget; runs a trace in real time on the calling
+    thread."""
+
+    def __init__(self, plans, budget_bytes: int = 8 << 30, streams: int = 4, max_batch: int = 256):
+        self._plans = list(plans)
+        self._arr = _plan_array(self._plans)
+        h = ctypes.c_void_p()
+        _check(lib.rklt_server_create(ctypes.cast(self._arr, ctypes.c_void_p), len(self._plans), budget_bytes, streams,
+                                      max_batch, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, reqs, mode: int = 0, recon=None, coef=None):
+        """reqs: RklTRequest array; recon / coef: optional lists of host arrays (numpy,
+        contiguous) receiving each request's outputs.  Returns (RklTResult array, wall_s)."""
+        n = len(reqs)
+        res = (RklTResult * max(n, 1))()
+        wall = ctypes.c_double()
+        pr = pc = None
+        if recon is not None:
+            pr = (ctypes.c_void_p * n)(*[a.ctypes.data if a is not None else None for a in recon])
+        if coef is not None:
+            pc = (ctypes.c_void_p * n)(*[a.ctypes.data if a is not None else None for a in coef])
+        _check(lib.rklt_server_run(self._h, ctypes.cast(reqs, ctypes.c_void_p), n, mode,
+                                   ctypes.cast(pr, ctypes.c_void_p) if pr is not None else None,
+                                   ctypes.cast(pc, ctypes.c_void_p) if pc is not None else None,
+                                   ctypes.cast(res, ctypes.c_void_p), ctypes.byref(wall)))
+        return res, wall.value
+
+    def close(self):
+        if self._h:
+            lib.rklt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rklt_server_create(plans, budget_bytes: int = 8 << 30, streams: int = 4, max_batch: int = 256) -> NativeServer:
+    return NativeServer(plans, budget_bytes, streams, max_batch)

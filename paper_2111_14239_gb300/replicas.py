@@ -18,8 +18,10 @@ def world() -> tuple:
 
 def image_seeds(base_seed: int, n_per_rank: int, rank: int) -> list:
     """Seeds of this rank's images: rank r takes base + r*n .. base + r*n + n - 1, so
-    ranks never share an image and rank 0 alone reproduces the single-GPU workload."""
-    return [base_seed + rank * n_per_rank + i for i in range(n_per_rank)]
+    ranks never share an image and rank 0 alone reproduces the single-GPU workload
+    (the rule lives with the input generators, synth_inputs.rank_seeds)."""
+    import synth_inputs
+    return synth_inputs.rank_seeds(base_seed, n_per_rank, rank)
 
 
 def shard(n_items: int, rank: int, world_size: int) -> range:

@@ -107,6 +107,13 @@ def sweep_batch(n: int = 256, side: int = 512, base_seed: int = 1000):
     return imgs, rhos
 
 
+def rank_seeds(base_seed: int, n_per_rank: int, rank: int) -> list:
+    """Seeds of one rank's images when each process of a multi-GPU run takes its own
+    images: rank r takes base + r*n .. base + r*n + n - 1, so ranks never share an
+    image and rank 0 alone reproduces the single-GPU workload."""
+    return [base_seed + rank * n_per_rank + i for i in range(n_per_rank)]
+
+
 def roofline_batch(n: int = 16, side: int = 4096, base_seed: int = 2000) -> np.ndarray:
     """Bandwidth workload: n images of side x side, rho = 0.95."""
     return ar1_batch(n, side, side, 0.95, base_seed)

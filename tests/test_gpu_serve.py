@@ -28,6 +28,8 @@ def _pool(n=12, seed=77):
 
 
 def test_continuous_batching_results_equal_alone(serve, orc):
+    """The native loop's continuous batching: every sampled result equals the same
+    request run alone through rklt_fused_items (bit for bit) and the oracle."""
     import paper_2111_14239_gb300 as rk
     pool = _pool()
     trace = serve.make_trace(800.0, 0.3, pool, seed=3)
@@ -66,3 +68,26 @@ def test_budget_admission(serve):
         2048, 2048, r.r)) > need_big // 2)
     assert stats["rejected"] == n_big
     assert all(not math.isnan(r.psnr) for r in trace if r.image is not big)
+
+
+def test_plain_loop_matches_continuous(serve, orc):
+    """One request at a time (rklt_fused per request) on the same trace: every
+    request completes after it arrives, and its SSE agrees with the continuous
+    loop's (a different kernel: within the FP32 bar) and with the oracle."""
+    pool = _pool(8, seed=11)
+    srv = serve.Server(RHOS, budget_bytes=64 << 20, streams=2)
+    t1 = serve.make_trace(500.0, 0.2, pool, seed=21)
+    t2 = serve.make_trace(500.0, 0.2, pool, seed=21)
+    s1 = srv.run(t1, keep_outputs=True)
+    s2 = srv.run(t2, keep_outputs=True, mode=serve.PLAIN)
+    assert s1["requests"] == s2["requests"] == len(t1) and s2["rejected"] == 0
+    for a, b in zip(t1, t2):
+        assert b.done >= b.arrival and b.status == 0
+        assert abs(a.sse - b.sse) <= 2.3e-4 * max(a.sse, 1e-30) or abs(a.sse - b.sse) < 1e-6
+        diff = np.abs(a.recon.astype(np.int64) - b.recon.astype(np.int64))
+        assert diff.max(initial=0) <= 1
+    for b in t2[:: max(1, len(t2) // 6)]:
+        op = orc.Plan(8, RHOS[b.plan])
+        sref, _, _ = orc.pipeline(8, op.That, b.image, b.r)
+        if sref > 0 and 10 * math.log10(255 ** 2 * b.image.size / sref) < 60:
+            assert abs(b.sse - sref) <= 2.3e-4 * sref
