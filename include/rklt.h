@@ -363,9 +363,11 @@ rklt_status rklt_rsweep(const rklt_plan *const *plans, int nplans, const uint8_t
  * binary32: w_ij = fl32(s_i s_j / Q_ij), q = fl32(fl32(C_ij) w_ij), Bbar =
  * floor(q + 1/2) -- the same steps on any hardware, so Bbar is reproducible bit
  * for bit.  Images as rklt_fused_batched (img_stride, recon_stride ignored when
- * nimg = 1), nimg in [1, 65535].  N in {4, 8}, rounded plans only.  Runs in the
- * fused pass's tile pipeline (TMA when pointers and pitches are 16-byte aligned).
- * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED (N = 16, 32, or an
+ * nimg = 1), nimg in [1, 65535].  N in {4, 8, 16, 32}, rounded plans only.  Runs
+ * in the fused pass's tile pipeline (TMA when pointers and pitches are 16-byte
+ * aligned); for N = 16, 32 with small supports on the tensor cores, where C is the
+ * same exact integer and the decision the same binary32 steps.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_UNSUPPORTED (an
  * exact-KLT / DCT plan), RKLT_ERR_OOM, RKLT_ERR_CUDA. */
 rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_img, int nimg, int H, int W, int64_t ld,
                              int64_t img_stride, int r, const double *h_Q, int32_t *d_qcoef, uint8_t *d_recon,

@@ -62,7 +62,7 @@ constexpr int REG_DMAX8 = 5;     // N = 8: two-CTA register path up to this diag
 constexpr int REG8_FULL = 5;     // variant number of the N = 8 register path for any D (one CTA per SM)
 constexpr int REG_REAL = 6;      // variant number of the register path for real (exact KLT / DCT) plans
 constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit on waits for copies already in flight
-constexpr int QV = 8;            // added to a variant number (N = 4, 8): quantised coefficients
+constexpr int QV = 8;            // added to a variant number: quantised coefficients
 __host__ __device__ constexpr int vbase(int V) { return V & 7; }
 
 // The quantiser's integer decision for one retained C (binary32, no contraction).
@@ -840,7 +840,7 @@ namespace rklt {
 //   N >= 16 otherwise: 1, 2, 3 = cooperative path (all block-rows at once) sized for
 //   Dr <= N/4, N/2, N;  real (exact KLT / DCT) plans: REG_REAL for N = 4 and for N = 8
 //   with D <= REG_DMAX8, else 1 = cooperative path block-row by block-row.
-// QV is added for the quantised form (N = 4, 8).
+// QV is added for the quantised form.
 __host__ __device__ inline int fused_variant(int N, int D) {
     if (N == 4) return 0;
     if (N == 8) return D <= REG_DMAX8 ? 0 : REG8_FULL;
@@ -860,8 +860,8 @@ __host__ __device__ inline int real_variant(int N, int D) {
 }
 
 // Consumer threads of kernel variant V, and the CTAs per SM its registers are sized for.
-__host__ __device__ constexpr int ncons(int V) { return V == TC_V ? NCONS_TC : NCONS; }
-__host__ __device__ constexpr int kminb(int V) { return vbase(V) == REG8_FULL ? 1 : (V == TC_V ? 3 : 2); }
+__host__ __device__ constexpr int ncons(int V) { return vbase(V) == TC_V ? NCONS_TC : NCONS; }
+__host__ __device__ constexpr int kminb(int V) { return vbase(V) == REG8_FULL ? 1 : (vbase(V) == TC_V ? 3 : 2); }
 
 template <int N, int V>
 __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom &g, uint8_t *tile, const TileCoord &tc,
@@ -874,9 +874,10 @@ __device__ __forceinline__ float process_tile(const PlanK<N> &P, const FusedGeom
         else if constexpr (N == 8 && VB == REG8_FULL) return tile_reg8_full<Q>(P, g, tile, tc, ct, Zs);
         else return tile_coop<N, Q>(P, g, tile, tc, ct, Ys, Zs);
     } else {
-        if constexpr (V == 1) return tile_coop2<N, N / 4>(P, g, tile, tc, ct, Ys, Zs);
-        else if constexpr (V == 2) return tile_coop2<N, N / 2>(P, g, tile, tc, ct, Ys, Zs);
-        else return tile_coop2<N, N>(P, g, tile, tc, ct, Ys, Zs);
+        constexpr bool Q = V >= QV;
+        if constexpr (vbase(V) == 1) return tile_coop2<N, N / 4, Q>(P, g, tile, tc, ct, Ys, Zs);
+        else if constexpr (vbase(V) == 2) return tile_coop2<N, N / 2, Q>(P, g, tile, tc, ct, Ys, Zs);
+        else return tile_coop2<N, N, Q>(P, g, tile, tc, ct, Ys, Zs);
     }
 }
 
@@ -915,7 +916,7 @@ __device__ __forceinline__ void tile_origin(const TileCoord &t, int &x, int &y, 
 // two 64 x 128 halves in the 128-byte swizzled layout.
 template <int V>
 __device__ __forceinline__ int tile_off(int y, int x) {
-    if constexpr (V == TC_V) return swz_off(y, x);
+    if constexpr (vbase(V) == TC_V) return swz_off(y, x);
     else return y * TW + x;
 }
 
@@ -924,7 +925,7 @@ __device__ __forceinline__ int tile_off(int y, int x) {
 template <int V>
 __device__ __forceinline__ void load_tile(const CUtensorMap *map, const FusedGeom &g, int x, int y, int z,
                                           uint8_t *dst, uint64_t *bar) {
-    if constexpr (V == TC_V) {
+    if constexpr (vbase(V) == TC_V) {
         const bool two = x + TW / 2 < g.W;
         mbar_arrive_expect_tx(bar, two ? TILE_BYTES : TC_HALF);
         tma_load_3d(dst, map, x, y, z, bar);
@@ -939,7 +940,7 @@ template <int V>
 __device__ __forceinline__ void store_tile(const CUtensorMap *map, const FusedGeom &g, int x, int y, int z,
                                            const uint8_t *src) {
     tma_store_3d(map, x, y, z, src);
-    if constexpr (V == TC_V) {
+    if constexpr (vbase(V) == TC_V) {
         if (x + TW / 2 < g.W) tma_store_3d(map, x + TW / 2, y, z, src + TC_HALF);
     }
 }
@@ -1067,14 +1068,14 @@ __global__ void __launch_bounds__(ncons(V) + 32, kminb(V))
         ((reinterpret_cast<uintptr_t>(g.recon) | uintptr_t(g.ld_recon) | uintptr_t(g.recon_stride)) & 7) == 0;
     // the cooperative path synchronises the consumer warps with named barriers, so
     // they must give up together; the register path has no such barrier
-    constexpr bool coop = vbase(V) != 0 && V != TC_V;
+    constexpr bool coop = vbase(V) != 0 && vbase(V) != TC_V;
     TcLane tcl;
     uint4 *tctab = reinterpret_cast<uint4 *>(Zs + (NC / 32) * TC_ZS);
     const uint32_t tctabl = smem_u32(tctab) + 16 * (tid & 31);
     const uint32_t tczs = smem_u32(Zs + (tid >> 5) * TC_ZS);
-    if constexpr (V == TC_V) {
-        if constexpr (N == 32) tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7);
-        else tc16_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7);
+    if constexpr (vbase(V) == TC_V) {
+        if constexpr (N == 32) tc_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7, V >= QV);
+        else tc16_setup(P, tcl, tctab, tid < 32, tid & 31, g.r, (tid >> 5) & 7, V >= QV);
         named_sync(1, NC);  // the table is written before any warp reads it
     }
     int64_t it = 0;
@@ -1120,14 +1121,15 @@ __global__ void __launch_bounds__(ncons(V) + 32, kminb(V))
             named_sync(1, NC);
         }
         float v;
-        if constexpr (V == TC_V) {
+        if constexpr (vbase(V) == TC_V) {
             // the benchmark configuration (coefficients 16-byte aligned with r % 4 == 0,
             // and the reconstruction) runs a copy with those branches resolved
+            constexpr bool Q = V >= QV;
             const bool fast = g.zcoef != nullptr && g.recon != nullptr && g.coef_vec4;
-            if constexpr (N == 32) v = fast ? tile_tc<true>(tcl, tctabl, g, buf, cw.c, tid, tczs)
-                                            : tile_tc<false>(tcl, tctabl, g, buf, cw.c, tid, tczs);
-            else v = fast ? tile_tc16<true>(tcl, tctabl, g, buf, cw.c, tid, tczs)
-                          : tile_tc16<false>(tcl, tctabl, g, buf, cw.c, tid, tczs);
+            if constexpr (N == 32) v = fast ? tile_tc<true, Q>(tcl, tctabl, g, buf, cw.c, tid, tczs)
+                                            : tile_tc<false, Q>(tcl, tctabl, g, buf, cw.c, tid, tczs);
+            else v = fast ? tile_tc16<true, Q>(tcl, tctabl, g, buf, cw.c, tid, tczs)
+                          : tile_tc16<false, Q>(tcl, tctabl, g, buf, cw.c, tid, tczs);
         }
         else v = process_tile<N, V>(P, g, buf, cw.c, tid, Ys, Zs);
         if (g.use_tma) {
@@ -1254,19 +1256,17 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
     // quantised call: the plan's constants plus this call's quantiser tables
     PlanK<N> pq;
     const PlanK<N> *pk = &plan.kparams<N>();
-    if constexpr (N <= 8) {
-        if (a.Q) {
-            V += QV;
-            pq = *pk;
-            for (int i = 0; i < N; i++)
-                for (int j = 0; j < N; j++) {
-                    pq.qw[i][j] = float(plan.s[i] * plan.s[j] / a.Q[i * N + j]);
-                    pq.qt[i][j] = float(a.Q[i * N + j] / (plan.s[i] * plan.s[j]));
-                }
-            pk = &pq;
-        }
+    if (a.Q) {
+        V += QV;
+        pq = *pk;
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++) {
+                pq.qw[i][j] = float(plan.s[i] * plan.s[j] / a.Q[i * N + j]);
+                pq.qt[i][j] = float(a.Q[i * N + j] / (plan.s[i] * plan.s[j]));
+            }
+        pk = &pq;
     }
-    const bool swz = V == TC_V;
+    const bool swz = vbase(V) == TC_V;
     const int box_w = swz ? TW / 2 : TW;
     CUtensorMap tin{}, tout{};
     if (tma) {
@@ -1295,13 +1295,19 @@ rklt_status launch_fused(const Plan &plan, const FusedArgs &a, cudaStream_t st) 
             default: fn = reinterpret_cast<const void *>(fused_kernel<8, QV + REG8_FULL>); break;
         }
     } else {
-        fn = V == 1 ? reinterpret_cast<const void *>(fused_kernel<N, 1>)
-                    : (V == 2 ? reinterpret_cast<const void *>(fused_kernel<N, 2>)
-                              : reinterpret_cast<const void *>(fused_kernel<N, 3>));
-        if (V == TC_V) fn = reinterpret_cast<const void *>(fused_kernel<N, TC_V>);
+        switch (V) {
+            case 1: fn = reinterpret_cast<const void *>(fused_kernel<N, 1>); break;
+            case 2: fn = reinterpret_cast<const void *>(fused_kernel<N, 2>); break;
+            case 3: fn = reinterpret_cast<const void *>(fused_kernel<N, 3>); break;
+            case TC_V: fn = reinterpret_cast<const void *>(fused_kernel<N, TC_V>); break;
+            case QV + 1: fn = reinterpret_cast<const void *>(fused_kernel<N, QV + 1>); break;
+            case QV + 2: fn = reinterpret_cast<const void *>(fused_kernel<N, QV + 2>); break;
+            case QV + 3: fn = reinterpret_cast<const void *>(fused_kernel<N, QV + 3>); break;
+            default: fn = reinterpret_cast<const void *>(fused_kernel<N, QV + TC_V>); break;
+        }
     }
     const int dev = ensure_smem_attr(fn);
-    const int threads = (V == TC_V ? NCONS_TC : NCONS) + 32;
+    const int threads = ncons(V) + 32;
     int per_sm = occupancy(fn, threads, L.total);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(g.ntiles, int64_t(per_sm) * sm_count(dev));

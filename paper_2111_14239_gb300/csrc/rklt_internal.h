@@ -37,8 +37,8 @@ struct PlanK {
     float sij[N][N];      // s_i * s_j (B = sij o C), rounded once from FP64
     float s[N];           // s_i
     uint32_t T2[N][N / 2]; // T[i][j] as a packed pair of IEEE halves (both lanes equal)
-    // JPEG-like quantiser of one call (N <= 8; filled per launch, zero in the plan):
-    static constexpr int QN = N <= 8 ? N : 1;
+    // JPEG-like quantiser of one call (filled per launch, zero in the plan):
+    static constexpr int QN = N;
     float qw[QN][QN];      // fl32(s_i s_j / Q_ij): Bbar = floor(fl32(C qw) + 1/2)
     float qt[QN][QN];      // fl32(Q_ij / (s_i s_j)): the dequantised value in the C domain
     // Parseval form of a rounded plan whose T T^T is diagonal (N <= 8; zero otherwise).

@@ -1,5 +1,5 @@
 // rklt_quant.cu -- JPEG-like quantisation with S absorbed into the quantiser
-// (Appendix of arXiv 2111.14239): for every N x N block (N = 4, 8)
+// (Appendix of arXiv 2111.14239): for every N x N block (N = 4, 8, 16, 32)
 //   C    = T A T^T                     exact integers (FP32 sums below 2^24)
 //   Bbar = round(C / Qtilde)           Qtilde = Q / (s s^T), round(x) = floor(x + 1/2)
 //   B'   = Bbar o Q                    the decoder's dequantised coefficients
@@ -8,7 +8,8 @@
 // per-image SSE / PSNR as in the fused pass.
 //
 // This file validates the call; the work runs in the fused kernel's quantised
-// variants (rklt_fused_impl.cuh): the same TMA tile pipeline, with the integer
+// variants (rklt_fused_impl.cuh; for N = 16, 32 the tensor-core and cooperative
+// paths, rklt_tc.cuh): the same TMA tile pipeline, with the integer
 // decision fixed in binary32 there: w_ij = fl32(s_i s_j / Q_ij) (FP64 quotient
 // rounded once, on the host), q = fl32(C_ij * w_ij) (no contraction),
 // Bbar = floor(q + 1/2) (exact for |q| < 2^22).
@@ -26,7 +27,6 @@ extern "C" rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_
     const Plan &p = plan->p;
     const int N = p.N;
     if (p.kind != 0) return fail(RKLT_ERR_UNSUPPORTED, "quantisation with S absorbed needs a rounded (integer) plan");
-    if (N != 4 && N != 8) return fail(RKLT_ERR_UNSUPPORTED, "quantisation is built for N = 4 and N = 8");
     if (!h_Q) return fail(RKLT_ERR_ARG, "h_Q is NULL");
     for (int k = 0; k < N * N; k++)
         if (!(h_Q[k] > 0.0) || !std::isfinite(h_Q[k])) return fail(RKLT_ERR_ARG, "Q entries must be positive and finite");
@@ -58,6 +58,12 @@ extern "C" rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_
     a.psnr = d_psnr;
     a.force_plain = transport_mode() == 1;
     a.Q = h_Q;
+    a.engine = 0;   // the quantised N = 32 path runs on the warp-level tensor-core engine
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return N == 4 ? launch_fused_n4(p, a, st) : launch_fused_n8(p, a, st);
+    switch (N) {
+        case 4: return launch_fused_n4(p, a, st);
+        case 8: return launch_fused_n8(p, a, st);
+        case 16: return launch_fused_n16(p, a, st);
+        default: return launch_fused_n32(p, a, st);
+    }
 }

@@ -141,8 +141,10 @@ struct TcLane {
 //   k = 10, 11  F1 A fragments of k-step k - 10: T[j][x], rows j = 2g (even), 2g + 1 (odd)
 //   k = 12    F2 B: 2^-12 T[i][y] (y < 16) for i = 2g (even n-tile), then i = 2g + 1
 //   k = 13, 14  lo digits: I1 n-tile k - 13 (even i, odd i), then I2 n-tile k - 13
-constexpr int TC_TAB = 15;
-constexpr int TC_TAB_BYTES = 15 * 32 * 16;   // the larger of the two tables
+//   k = 15, 16  (quantised calls) 2^12 w_ij of those elements, w = fl32(s_i s_j / Q_ij)
+//   k = 17, 18  (quantised calls) 2^-12 fl32(Q_ij / (s_i s_j))
+constexpr int TC_TAB = 19;
+constexpr int TC_TAB_BYTES = 19 * 32 * 16;   // the larger of the two tables
 
 __device__ __forceinline__ float tc_T(const PlanK<32> &P, int i, int x) {
     return x < 16 ? P.T[i][x] : ((i & 1) ? -P.T[i][31 - x] : P.T[i][31 - x]);
@@ -152,7 +154,7 @@ __device__ __forceinline__ float tc_T(const PlanK<32> &P, int i, int x) {
 // Element q = 4 * nt + e of a lane's F2 accumulator holds C[i][j] with
 // j = 2g + (e >> 1) and i = 4t + 2 (e & 1) + nt.  bx is the warp's block column.
 __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool write_tab, int lane, int r,
-                                int bx) {
+                                int bx, bool quant) {
     const int g = lane >> 2, t = lane & 3;
     const int j0 = 2 * g, j1 = 2 * g + 1;
     float s0 = 0.0f, s1 = 0.0f;
@@ -198,7 +200,7 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
         tab[(2 + nt) * 32 + lane] = make_uint4(h4e, h4e, h4o, h4o);
         tab[(13 + nt) * 32 + lane] = make_uint4(l3e, l3o, l4e, l4o);
     }
-    uint32_t zp[8], bs[8], kp[8];
+    uint32_t zp[8], bs[8], kp[8], qw[8], qt[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const int nt = q >> 2, e = q & 3;
@@ -207,13 +209,26 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
         zp[q] = uint32_t(4 * (z < r ? z : TC_ZS - 1));
         bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
         kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
+        qw[q] = __float_as_uint(4096.0f * P.qw[i][j]);
+        qt[q] = __float_as_uint(P.qt[i][j] * (1.0f / 4096.0f));
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         tab[(4 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
         tab[(6 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
         tab[(8 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
+        if (quant) {
+            tab[(15 + h) * 32 + lane] = make_uint4(qw[4 * h], qw[4 * h + 1], qw[4 * h + 2], qw[4 * h + 3]);
+            tab[(17 + h) * 32 + lane] = make_uint4(qt[4 * h], qt[4 * h + 1], qt[4 * h + 2], qt[4 * h + 3]);
+        }
     }
+}
+
+// The quantiser's integer decision on an F2 accumulator element d = C 2^-12 with
+// the table value w12 = 2^12 w: fl32(d w12) = fl32(C w) exactly (scaling by powers of
+// two), then floor(fl32(q + 1/2)) -- the binary32 decision of the register path.
+__device__ __forceinline__ float tc_quant_code(float d, uint32_t w12) {
+    return floorf(__fadd_rn(__fmul_rn(d, __uint_as_float(w12)), 0.5f));
 }
 
 // One 32 x 32 block by one warp: `blk` is the shared-window address of the tile
@@ -221,7 +236,7 @@ __device__ inline void tc_setup(const PlanK<32> &P, TcLane &c, uint4 *tab, bool 
 // staging buffer (shared-window address).  Returns the lane's share of the block's
 // SSE; writes the 8-bit reconstruction in place when `recon`, and the r normalised
 // coefficients to zg (if not null).
-template <bool FAST>
+template <bool FAST, bool Q = false>
 __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, int r,
                                             float *zg, uint32_t zs, bool recon_, bool vec4_) {
     // FAST: coefficients (16-byte aligned, r % 4 == 0) and reconstruction both wanted
@@ -283,7 +298,23 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
     uint32_t ch[2][2], cl[2][2];
 #pragma unroll
     for (int nt = 0; nt < 2; nt++) {
-        if (FAST || zg) {
+        if constexpr (Q) {
+            // quantised: Bbar (int32) where the coefficients go; C' = Bbar Qtilde 2^-12
+            const uint4 qw = lds128(tabl + (15 + nt) * 512), qt = lds128(tabl + (17 + nt) * 512);
+            const float b0 = tc_quant_code(d2[nt][0], qw.x), b1 = tc_quant_code(d2[nt][1], qw.y);
+            const float b2 = tc_quant_code(d2[nt][2], qw.z), b3 = tc_quant_code(d2[nt][3], qw.w);
+            if (FAST || zg) {
+                const uint4 zp = lds128(tabl + (4 + nt) * 512);
+                sts_f32(zs + zp.x, __int_as_float(int(b0)));
+                sts_f32(zs + zp.y, __int_as_float(int(b1)));
+                sts_f32(zs + zp.z, __int_as_float(int(b2)));
+                sts_f32(zs + zp.w, __int_as_float(int(b3)));
+            }
+            d2[nt][0] = __fmul_rn(b0, __uint_as_float(qt.x));
+            d2[nt][1] = __fmul_rn(b1, __uint_as_float(qt.y));
+            d2[nt][2] = __fmul_rn(b2, __uint_as_float(qt.z));
+            d2[nt][3] = __fmul_rn(b3, __uint_as_float(qt.w));
+        } else if (FAST || zg) {
             const uint4 zp = lds128(tabl + (4 + nt) * 512), bs = lds128(tabl + (6 + nt) * 512);
             sts_f32(zs + zp.x, __uint_as_float(bs.x) * d2[nt][0]);
             sts_f32(zs + zp.y, __uint_as_float(bs.y) * d2[nt][1]);
@@ -392,7 +423,7 @@ __device__ __forceinline__ float tc_block32(const TcLane &c, uint32_t tabl, uint
 // The 16 blocks of one tile: warp w takes block columns w and w + 4 of both block
 // rows.  Column w + 4 lies in the second 128-byte half of the tile at the same
 // swizzle phase, so its addresses are column w's plus TC_HALF.
-template <bool FAST>
+template <bool FAST, bool Q = false>
 __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                          const TileCoord &tc, int ct, uint32_t zs) {
     const int w = ct >> 5, lane = ct & 31;
@@ -408,8 +439,8 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
         if (w + 4 * cg >= nb_in) break;
         for (int by = 0; by < rows_in; by++) {
             float *zg = zt ? zt + (int64_t(by) * bw + 4 * cg) * g.r : nullptr;
-            sse += tc_block32<FAST>(c, tabl, smem_u32(tile) + by * 32 * 128 + cg * TC_HALF, lane, g.r, zg, zs,
-                                    g.recon != nullptr, g.coef_vec4 != 0);
+            sse += tc_block32<FAST, Q>(c, tabl, smem_u32(tile) + by * 32 * 128 + cg * TC_HALF, lane, g.r, zg, zs,
+                                       g.recon != nullptr, g.coef_vec4 != 0);
         }
     }
     return sse;
@@ -440,7 +471,8 @@ __device__ __forceinline__ float tile_tc(const TcLane &c, uint32_t tabl, const F
 //   k = 8     I2 lo digits for n-tile 0, 1
 //   k = 9, 10   staging byte offsets 4 ((2 vb + hb) r + z) of accumulator elements q = 4 class + e
 //   k = 11, 12  2^12 s_i s_j;  k = 13, 14  1.0 when retained, else 0.0
-constexpr int TC16_TAB = 15;
+//   k = 15, 16 and 17, 18  (quantised calls) as for N = 32
+constexpr int TC16_TAB = 19;
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float tc16_T(const PlanK<16> &P, int i, int x) {
     return x < 8 ? P.T[i][x] : ((i & 1) ? -P.T[i][15 - x] : P.T[i][15 - x]);
@@ -450,7 +482,7 @@ __device__ __forceinline__ float tc16_Ti(const PlanK<16> &P, int l, int j) {  //
 }
 
 __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, bool write_tab, int lane, int r,
-                                  int bx) {
+                                  int bx, bool quant) {
     const int g = lane >> 2, t = lane & 3;
     float s0 = 0.0f;
     for (int x = 0; x < 16; x++) s0 += tc16_T(P, g, x);
@@ -500,7 +532,7 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
         tab[7 * 32 + lane] = make_uint4(ha, ha, hb2, hb2);
         tab[8 * 32 + lane] = make_uint4(la, lb, 0u, 0u);
     }
-    uint32_t zp[8], bs[8], kp[8];
+    uint32_t zp[8], bs[8], kp[8], qw[8], qt[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const int cls = q >> 2, e = q & 3;
@@ -510,19 +542,25 @@ __device__ inline void tc16_setup(const PlanK<16> &P, TcLane &c, uint4 *tab, boo
         zp[q] = uint32_t(4 * (z < r ? (2 * vb + hb) * r + z : TC_ZS - 1));
         bs[q] = __float_as_uint(4096.0f * P.sij[i][j]);
         kp[q] = __float_as_uint(z < r ? 1.0f : 0.0f);
+        qw[q] = __float_as_uint(4096.0f * P.qw[i][j]);
+        qt[q] = __float_as_uint(P.qt[i][j] * (1.0f / 4096.0f));
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         tab[(9 + h) * 32 + lane] = make_uint4(zp[4 * h], zp[4 * h + 1], zp[4 * h + 2], zp[4 * h + 3]);
         tab[(11 + h) * 32 + lane] = make_uint4(bs[4 * h], bs[4 * h + 1], bs[4 * h + 2], bs[4 * h + 3]);
         tab[(13 + h) * 32 + lane] = make_uint4(kp[4 * h], kp[4 * h + 1], kp[4 * h + 2], kp[4 * h + 3]);
+        if (quant) {
+            tab[(15 + h) * 32 + lane] = make_uint4(qw[4 * h], qw[4 * h + 1], qw[4 * h + 2], qw[4 * h + 3]);
+            tab[(17 + h) * 32 + lane] = make_uint4(qt[4 * h], qt[4 * h + 1], qt[4 * h + 2], qt[4 * h + 3]);
+        }
     }
 }
 
 // One 32 x 32 region (four 16 x 16 blocks) by one warp.  `in` has bit 2 vb + hb set
 // for the blocks inside the image (all four in the interior); only those add to the
 // SSE.  The staging buffer receives each block's r coefficients at (2 vb + hb) r.
-template <bool ALL_IN, bool FAST>
+template <bool ALL_IN, bool FAST, bool Q = false>
 __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uint32_t blk, int lane, uint32_t zs,
                                              bool coef_, bool recon_, int in) {
     const bool coef = FAST || coef_, recon = FAST || recon_;
@@ -579,7 +617,22 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
     uint32_t ch[2][2], cl[2][2];
 #pragma unroll
     for (int cls = 0; cls < 2; cls++) {
-        if (coef) {
+        if constexpr (Q) {
+            const uint4 qw = lds128(tabl + (15 + cls) * 512), qt = lds128(tabl + (17 + cls) * 512);
+            const float b0 = tc_quant_code(d2[cls][0], qw.x), b1 = tc_quant_code(d2[cls][1], qw.y);
+            const float b2 = tc_quant_code(d2[cls][2], qw.z), b3 = tc_quant_code(d2[cls][3], qw.w);
+            if (coef) {
+                const uint4 zp = lds128(tabl + (9 + cls) * 512);
+                sts_f32(zs + zp.x, __int_as_float(int(b0)));
+                sts_f32(zs + zp.y, __int_as_float(int(b1)));
+                sts_f32(zs + zp.z, __int_as_float(int(b2)));
+                sts_f32(zs + zp.w, __int_as_float(int(b3)));
+            }
+            d2[cls][0] = __fmul_rn(b0, __uint_as_float(qt.x));
+            d2[cls][1] = __fmul_rn(b1, __uint_as_float(qt.y));
+            d2[cls][2] = __fmul_rn(b2, __uint_as_float(qt.z));
+            d2[cls][3] = __fmul_rn(b3, __uint_as_float(qt.w));
+        } else if (coef) {
             const uint4 zp = lds128(tabl + (9 + cls) * 512), bs = lds128(tabl + (11 + cls) * 512);
             sts_f32(zs + zp.x, __uint_as_float(bs.x) * d2[cls][0]);
             sts_f32(zs + zp.y, __uint_as_float(bs.y) * d2[cls][1]);
@@ -662,7 +715,7 @@ __device__ __forceinline__ float tc16_region(const TcLane &c, uint32_t tabl, uin
 
 // The 16 regions of one tile (N = 16): warp w takes region columns w and w + 4 (the
 // latter TC_HALF further in the swizzled tile) of both region rows.
-template <bool FAST>
+template <bool FAST, bool Q = false>
 __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const FusedGeom &g, uint8_t *tile,
                                            const TileCoord &tc, int ct, uint32_t zs) {
     const int lane = ct & 31;
@@ -683,8 +736,8 @@ __device__ __forceinline__ float tile_tc16(const TcLane &c, uint32_t tabl, const
         const bool rows2 = 2 * ry + 1 < rows_in;
         const int in = (rows2 && cols2) ? 15 : (1 | (cols2 ? 2 : 0) | (rows2 ? 4 | (cols2 ? 8 : 0) : 0));
         const uint32_t blk = t32 + ry * 32 * 128;
-        if (in == 15) sse += tc16_region<true, FAST>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
-        else sse += tc16_region<false, FAST>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        if (in == 15) sse += tc16_region<true, FAST, Q>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
+        else sse += tc16_region<false, FAST, Q>(c, tabl, blk, lane, zs, coef, g.recon != nullptr, in);
         if (coef) {
             // coefficients of the region's first block
             float *zrow0 = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(tc.ty * (TH / 16) + 2 * ry) * bw +

@@ -164,10 +164,13 @@ def test_batch_workload_sampled(rk, orc):
         check_recon_u8(bufs[k][1].cpu().numpy(), rref, 8)
 
 
-def test_quant_workload_sampled(rk, orc, roofline):
+@pytest.mark.parametrize("n,r", [(8, 64), (32, 128), (16, 32)])
+def test_quant_workload_sampled(rk, orc, roofline, n, r):
+    """Quantised coefficients bit-exact on sampled blocks of the 16 x 4096^2 batch:
+    N = 8 with every coefficient (full-block register path), N = 32 and 16 at
+    r = N^2/8 (tensor-core path)."""
     imgs, d = roofline
     nimg, H, W = imgs.shape
-    n, r = 8, 64
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     Q = 2.0 + 3.0 * (i + j)
     plan = rk.rklt_make(n, 0.95)

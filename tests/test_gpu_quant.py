@@ -50,14 +50,19 @@ def run(rk, plan, img, r, Q, nimg_axis=False):
             ps.cpu().numpy())
 
 
-@pytest.mark.parametrize("n,rho", [(8, 0.95), (8, 0.5), (4, 0.95)])
+SHAPES = {4: (196, 548), 8: (200, 552), 16: (208, 560), 32: (224, 576)}
+
+
+@pytest.mark.parametrize("n,rho", [(8, 0.95), (8, 0.5), (4, 0.95), (16, 0.95), (32, 0.95), (16, 0.5)])
 def test_quant_against_oracle(rk, orc, n, rho):
-    H, W = (200, 552) if n == 8 else (196, 548)
+    """Bbar bit-exact against the oracle; for N = 16, 32 r = N^2/8 runs on the tensor
+    cores and r = N^2/4, N^2 on the cooperative path."""
+    H, W = SHAPES[n]
     img = si.ar1_image(H, W, 0.95, 70 + n)
     plan = rk.rklt_make(n, rho)
     p = orc.Plan(n, rho)
     for qname, Q in quantisers(n).items():
-        for r in (1, n * n // 4, n * n):
+        for r in sorted({1, n * n // 8, n * n // 4, n * n}):
             qc, rec, sse, ps = run(rk, plan, img, r, Q)
             sse_ref, qc_ref, rec_ref = orc.quant_pipeline(n, p.T, p.s, Q, img, r, want_coef=True, want_recon=True)
             assert np.array_equal(qc[0], qc_ref), f"{qname} r={r}: {np.count_nonzero(qc[0] != qc_ref)} differ"
@@ -99,19 +104,19 @@ def test_quant_rejects(rk):
     d = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
     s = torch.zeros(1, dtype=torch.float64, device="cuda")
     ps = torch.zeros(1, device="cuda")
-    for plan, Q, status in ((rk.rklt_make(16, 0.95), np.ones((16, 16)), 8),
-                            (rk.rklt_make_dct(8), np.ones((8, 8)), 8),
+    for plan, Q, status in ((rk.rklt_make_dct(8), np.ones((8, 8)), 8),
+                            (rk.rklt_make_klt(16, 0.95), np.ones((16, 16)), 8),
                             (rk.rklt_make(8, 0.95), np.zeros((8, 8)), 1)):
         with pytest.raises(rk.RklTError) as e:
             rk.rklt_fused_quant(plan, d, 10, Q, s, ps)
         assert e.value.status == status
 
 
-@pytest.mark.parametrize("n", [4, 8])
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
 def test_quant_tma_ragged_and_plain_transport(rk, orc, n):
     """16-byte aligned rows (TMA tiles) with ragged edges in both directions, against the
     oracle, and bit-identical to the plain-load transport of the same call."""
-    H, W = (200, 1040) if n == 8 else (196, 1040)
+    H, W = {4: (196, 1040), 8: (200, 1040), 16: (208, 1040), 32: (224, 1056)}[n]
     img = si.ar1_image(H, W, 0.9, 110 + n)
     plan = rk.rklt_make(n, 0.95)
     p = orc.Plan(n, 0.95)
