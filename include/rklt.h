@@ -388,16 +388,16 @@ rklt_status rklt_mssim(const uint8_t *d_x, const uint8_t *d_y, int nimg, int H, 
 /* rklt_fused for callers that must not allocate.  (Not part of the paper: this
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *
- * rklt_fused obtains a small per-call scratch buffer (one float per 64 x 256
- * tile, or per 32 x 256 strip when N = 32 and the retained support stays inside
- * i + j < 16) from a stream-ordered memory pool.  Some callers cannot allow that: code
+ * rklt_fused obtains a small per-call scratch buffer (one error partial of 4 or
+ * 8 bytes per 64 x 256 tile, or per 32 x 256 strip when N = 32 and the retained
+ * support stays inside i + j < 16) from a stream-ordered memory pool.  Some callers cannot allow that: code
  * running on a real-time path where an allocation may block or synchronise the
  * device, plugins whose host framework owns the whole device-memory budget and
  * leaves no room for a private pool, and callers that must keep every device
  * allocation under their own bookkeeping.  This entry point allocates nothing: no
  * cudaMalloc, cudaFree, pool or library allocation.  Its scratch is one fixed
- * array of 65536 floats (256 KB) inside the library's device image, which every
- * GPU that loads the library keeps until the process exits.
+ * array of 65536 eight-byte slots (512 KB) inside the library's device image,
+ * which every GPU that loads the library keeps until the process exits.
  *
  * Arguments, outputs and results are those of rklt_fused (bit-identical).
  * Limit: the image may span at most 65536 tiles (ceil(H/64) * ceil(W/256) <= 65536,

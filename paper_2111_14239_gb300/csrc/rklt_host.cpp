@@ -96,19 +96,60 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+namespace {
+
+// Recent tensor-map encodings: a descriptor is a pure function of its arguments, so
+// repeated calls on the same buffers (a serving or benchmark loop) reuse it instead
+// of encoding it again on the host.
+struct MapKey {
+    const void *base;
+    int W, H, nimg;
+    int64_t ld, stride;
+    int box_w, box_h;
+    bool swz;
+    bool operator==(const MapKey &o) const {
+        return base == o.base && W == o.W && H == o.H && nimg == o.nimg && ld == o.ld && stride == o.stride &&
+               box_w == o.box_w && box_h == o.box_h && swz == o.swz;
+    }
+};
+constexpr int kMapCache = 16;
+std::mutex g_map_mu;
+MapKey g_map_key[kMapCache];
+CUtensorMap g_map_val[kMapCache];
+int g_map_used = 0, g_map_next = 0;
+
+}  // namespace
+
 // 3-D uint8 tensor map (x = column, y = row, z = image) with a box_w x box_h x 1 box.
 bool make_map_u8(CUtensorMap *m, const void *base, int W, int H, int nimg, int64_t ld, int64_t stride, int box_w,
                  int box_h, bool swizzle128) {
+    const MapKey key{base, W, H, nimg, ld, stride, box_w, box_h, swizzle128};
+    {
+        std::lock_guard<std::mutex> lk(g_map_mu);
+        for (int k = 0; k < g_map_used; k++)
+            if (g_map_key[k] == key) {
+                *m = g_map_val[k];
+                return true;
+            }
+    }
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {cuuint64_t(W), cuuint64_t(H), cuuint64_t(nimg)};
     cuuint64_t strides[2] = {cuuint64_t(ld), cuuint64_t(stride)};
     cuuint32_t box[3] = {cuuint32_t(box_w), cuuint32_t(box_h), 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const bool ok = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (ok) {
+        std::lock_guard<std::mutex> lk(g_map_mu);
+        g_map_key[g_map_next] = key;
+        g_map_val[g_map_next] = *m;
+        g_map_next = (g_map_next + 1) % kMapCache;
+        if (g_map_used < kMapCache) g_map_used++;
+    }
+    return ok;
 }
 
 }  // namespace rklt

@@ -1,12 +1,12 @@
 // rklt_noalloc.cu -- rklt_fused without any allocation.
 //
-// rklt_fused takes its scratch (one float per 64 x 256 tile, or per 32 x 256 strip
-// for the N = 32 tensor-memory kernel; one 64-bit accumulator per image on the
+// rklt_fused takes its scratch (one error partial per 64 x 256 tile, or per 32 x 256
+// strip for the N = 32 tensor-memory kernel: a float, or a 64-bit integer on the
 // register path whose error comes from Parseval's identity) from a stream-ordered
 // memory pool.  This variant takes it from a fixed array in the library's own
 // device memory instead, so a call performs no allocation of any kind.  The array
 // is a file-scope __device__ object: every GPU that loads the library holds it
-// (256 KB) until the process exits.  Host code cannot pass the array's name to a
+// (512 KB) until the process exits.  Host code cannot pass the array's name to a
 // kernel -- on the host that name denotes a stand-in object, not device memory --
 // so its device address is looked up with cudaGetSymbolAddress, with the device
 // current, once per device and context.
@@ -20,7 +20,7 @@ namespace rklt {
 
 constexpr int64_t kNoAllocMaxTiles = 65536;  // 2^16 tiles: 2^30 pixels (2^29 for 32-row strips)
 
-static __device__ __align__(256) float g_noalloc_partials[kNoAllocMaxTiles];
+static __device__ __align__(256) unsigned long long g_noalloc_partials[kNoAllocMaxTiles];  // 8 bytes per tile
 
 namespace {
 
@@ -117,7 +117,7 @@ extern "C" rklt_status rklt_fused_noalloc(const rklt_plan *plan, const uint8_t *
     a.sse = d_sse;
     a.psnr = d_psnr;
     a.partials = partials;
-    a.scratch_cap = kNoAllocMaxTiles * int64_t(sizeof(float));
+    a.scratch_cap = kNoAllocMaxTiles * int64_t(sizeof(unsigned long long));
     a.force_plain = transport_mode() == 1;
     a.engine = engine;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

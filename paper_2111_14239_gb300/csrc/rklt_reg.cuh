@@ -332,6 +332,15 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
+// Sum of the NC / 32 consumer warps' tile errors.
+template <int NC>
+__device__ __forceinline__ uint64_t pars_red_sum(const uint64_t *w) {
+    uint64_t t = 0;
+#pragma unroll
+    for (int i = 0; i < NC / 32; i++) t += w[i];
+    return t;
+}
+
 // The blocks of one tile owned by consumer thread ct (NC consumers), B at a time;
 // errors added to acc.
 template <int N, int D, bool COEF, bool RECON, int NC, int B>
@@ -360,13 +369,6 @@ __device__ __forceinline__ void pars_tile(const PlanK<N> &P, const FusedGeom &g,
         }
         acc += pars_blocks<N, D, COEF, RECON, B>(P, w, blk, r, coef, act, g.coef_vec4);
     }
-}
-
-// Adds the warp's errors of image img to the per-image accumulator.
-__device__ __forceinline__ void pars_flush(const FusedGeom &g, int img, uint64_t acc) {
-    const uint64_t t = warp_sum_u64(acc);
-    if ((threadIdx.x & 31) == 0 && t != 0) atomicAdd(reinterpret_cast<unsigned long long *>(g.sse_acc + img),
-                                                     static_cast<unsigned long long>(t));
 }
 
 // Copies one tile into the shared buffer with plain loads (bytes outside the image
@@ -431,8 +433,9 @@ __device__ __forceinline__ void plain_tile_out(const FusedGeom &g, const TileCoo
 // ---------------------------------------------------------------------------
 // The kernel: warps 0..3 consume (PARS_B blocks per thread per step over the tile);
 // warp 4 is the TMA producer (idle with plain loads).  OUT: bit 0 coefficients,
-// bit 1 8-bit reconstruction.  Per-image errors go to g.sse_acc (u64, zeroed by the
-// launcher) as exact integers times m^2.
+// bit 1 8-bit reconstruction.  Each tile's error (an exact integer, times m^2) goes
+// to g.sse_acc[tile]: every tile is written exactly once, so the scratch needs no
+// clearing, and the per-image sums of exact integers do not depend on their order.
 // ---------------------------------------------------------------------------
 // Consumer threads per CTA and blocks per consumer step.  Two blocks per thread:
 // each constant operand load and each per-tile step serves two blocks, and a warp
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(PARS_NC + 32, 2)
     const int NST = g.stages;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (g.use_tma ? NST : 1) * TILE_BYTES);
     uint64_t *empty = full + STAGES;
+    uint64_t *red = empty + STAGES;   // [stage][consumer warp] tile errors
     const int tid = threadIdx.x;
 
     if (g.use_tma && tid == PNC) {
@@ -478,6 +482,7 @@ __global__ void __launch_bounds__(PARS_NC + 32, 2)
                     ok = false;
                     break;
                 }
+                g.sse_acc[tile - int64_t(NST) * gridDim.x] = pars_red_sum<PNC>(red + s * (PNC / 32));
                 if (RECON) {
                     int x, y, z;
                     tile_origin(sw.c, x, y, z);
@@ -503,6 +508,7 @@ __global__ void __launch_bounds__(PARS_NC + 32, 2)
                 if (!g.inject_stall) mbar_wait_bounded(&full[s], par, DRAIN_NS);
                 continue;
             }
+            g.sse_acc[int64_t(blockIdx.x) + j * gridDim.x] = pars_red_sum<PNC>(red + s * (PNC / 32));
             if (RECON) {
                 int x, y, z;
                 tile_origin(sw.c, x, y, z);
@@ -516,11 +522,9 @@ __global__ void __launch_bounds__(PARS_NC + 32, 2)
     }
 
     // ---------------- consumers ----------------
-    uint64_t acc = 0;
     int64_t it = 0;
     TileWalker cw;
     cw.init(g);
-    int cur = cw.c.img;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++it, cw.next(g)) {
         uint8_t *buf;
         int s = 0;
@@ -535,30 +539,40 @@ __global__ void __launch_bounds__(PARS_NC + 32, 2)
             plain_tile_in<PNC>(g, cw.c, buf, tid);
             named_sync(1, PNC);
         }
-        if (cw.c.img != cur) {  // uniform across the CTA
-            pars_flush(g, cur, acc);
-            acc = 0;
-            cur = cw.c.img;
-        }
+        uint64_t acc = 0;
         pars_tile<N, D, COEF, RECON, PNC, PARS_B>(P, g, buf, cw.c, tid, acc);
+        acc = warp_sum_u64(acc);
         if (g.use_tma) {
+            // warp errors -> red[s][warp]; the producer adds the four and writes the tile's
+            if ((tid & 31) == 0) red[s * (PNC / 32) + (tid >> 5)] = acc;
             if (RECON) fence_proxy_async_smem();
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&empty[s]);
-        } else if (RECON) {
+        } else {
+            if ((tid & 31) == 0) red[tid >> 5] = acc;
             named_sync(1, PNC);
-            plain_tile_out<PNC>(g, cw.c, buf, tid);
+            if (tid == 0) g.sse_acc[tile] = pars_red_sum<PNC>(red);
+            if (RECON) plain_tile_out<PNC>(g, cw.c, buf, tid);
         }
     }
-    pars_flush(g, cur, acc);
 }
 
-// Per image: SSE = acc / m^2 (exact quotient of exact integers, rounded once), PSNR.
-static __global__ void pars_finalize(const unsigned long long *acc, int nimg, int H, int W, double m2, double *sse,
-                                     float *psnr) {
-    const int img = blockIdx.x * blockDim.x + threadIdx.x;
+// Per image (one CTA each): the exact integer sum of its tiles' errors, then
+// SSE = sum / m^2 (exact quotient rounded once) and PSNR.
+static __global__ void pars_finalize(const unsigned long long *tiles, int64_t tiles_per_img, int nimg, int H, int W,
+                                     double m2, double *sse, float *psnr) {
+    __shared__ unsigned long long red[256 / 32];
+    const int img = blockIdx.x;
     if (img >= nimg) return;
-    const double s = double(acc[img]) / m2;
+    unsigned long long acc = 0;
+    for (int64_t t = threadIdx.x; t < tiles_per_img; t += blockDim.x) acc += tiles[int64_t(img) * tiles_per_img + t];
+    acc = warp_sum_u64(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned long long tot = 0;
+    for (int w = 0; w < int(blockDim.x) / 32; w++) tot += red[w];
+    const double s = double(tot) / m2;
     const double npx = double(H) * double(W);
     if (sse) sse[img] = s;
     if (psnr) {
@@ -632,8 +646,9 @@ rklt_status launch_pars(const Plan &plan, const FusedArgs &a, cudaStream_t st, P
     g.timeout_ns = wait_timeout_ns();
     g.inject_stall = inject_stall();
 
-    // scratch: one u64 error accumulator per image, zeroed on the stream
-    const size_t acc_bytes = size_t(a.nimg) * sizeof(unsigned long long);
+    // scratch: one u64 error per tile (each written once by the kernel)
+    const int64_t tiles_per_img = int64_t(g.tiles_x) * g.tiles_y;
+    const size_t acc_bytes = size_t(std::max<int64_t>(g.ntiles, 1)) * sizeof(unsigned long long);
     void *scratch = nullptr;
     if (a.partials) {
         if (int64_t(acc_bytes) > a.scratch_cap) return fail(RKLT_ERR_ARG, "scratch array too small for this call");
@@ -645,11 +660,7 @@ rklt_status launch_pars(const Plan &plan, const FusedArgs &a, cudaStream_t st, P
             return fail(RKLT_ERR_OOM, "scratch allocation failed");
         g.sse_acc = static_cast<unsigned long long *>(scratch);
     }
-    cudaError_t e = cudaMemsetAsync(g.sse_acc, 0, acc_bytes, st);
-    if (e != cudaSuccess) {
-        if (scratch) cudaFreeAsync(scratch, st);
-        return cuda_fail(e, "scratch clear");
-    }
+    cudaError_t e = cudaSuccess;
 
     const bool empty = a.H == 0 || a.W == 0;
     if (!empty) {
@@ -673,7 +684,7 @@ rklt_status launch_pars(const Plan &plan, const FusedArgs &a, cudaStream_t st, P
             if (scratch) cudaFreeAsync(scratch, st);
             return fail(RKLT_ERR_UNSUPPORTED, "register path: no kernel for this diagonal bound");
         }
-        const int smem = (tma ? g.stages : 1) * TILE_BYTES + 2 * STAGES * 8 + 1024;
+        const int smem = (tma ? g.stages : 1) * TILE_BYTES + 2 * STAGES * 8 + STAGES * (PARS_NC / 32) * 8 + 1024;
         const int dev = ensure_smem_attr(fn);
         int per_sm = occupancy(fn, nthreads, smem);
         if (per_sm < 1) per_sm = 1;
@@ -690,7 +701,8 @@ rklt_status launch_pars(const Plan &plan, const FusedArgs &a, cudaStream_t st, P
             return cuda_fail(e, "register-path kernel launch");
         }
     }
-    pars_finalize<<<(a.nimg + 127) / 128, 128, 0, st>>>(g.sse_acc, a.nimg, a.H, a.W, double(pk.pm2), a.sse, a.psnr);
+    pars_finalize<<<a.nimg, 256, 0, st>>>(g.sse_acc, empty ? 0 : tiles_per_img, a.nimg, a.H, a.W, double(pk.pm2),
+                                          a.sse, a.psnr);
     e = cudaGetLastError();
     if (scratch) cudaFreeAsync(scratch, st);
     return e == cudaSuccess ? RKLT_OK : cuda_fail(e, "register-path finalize launch");
