@@ -258,12 +258,24 @@ typedef struct rklt_batch rklt_batch;
 
 /* A reusable batch of rklt_fused_items work (Sec. 4.1 per image): the work queue
  * (library-owned device memory, freed by rklt_batch_destroy) is built once, the
- * launch sequence is captured into a CUDA graph and every rklt_batch_run replays it.  The device buffers named in h_items
- * and d_sse / d_psnr are baked into the graph: refill them between runs, keep
- * them alive until rklt_batch_destroy.  flags bit 0 = autotune: time a few launch
- * shapes (threads per CTA, CTAs per SM) on the batch itself and keep the fastest;
- * creation then runs the batch several times, overwriting its outputs.  Creation
- * synchronises the device.
+ * launch sequence is captured into a CUDA graph and every rklt_batch_run replays it.
+ * Two forms of the work exist: one persistent kernel over the whole flattened
+ * queue (every plan and r in one launch: units ordered heaviest first, dealt
+ * round-robin to the warps, each dispatching on its image's retained support, the
+ * per-image SSE / PSNR written by the warp that completes the image's last unit --
+ * the graph is then one kernel node), and one launch per (plan, support) group
+ * fanned over side streams.  flags bit 0 = autotune: time both forms in several
+ * launch shapes (threads per CTA, CTAs per SM) on the batch itself and keep the
+ * fastest (rklt_batch_candidates lists what was timed); without it the grouped form
+ * runs with 256 threads and one CTA per SM.  (On GB300 the grouped form measured
+ * about 2.4x faster for 2000 uneven crops: there each plan's tables are constant-bank
+ * operands of the arithmetic, while the queue form must load them by slot index.)  Creation then has run the batch
+ * several times, overwriting its outputs, and synchronises the device.  The queue
+ * form keeps each plan in a constant-memory slot of the device (16 per block size,
+ * written on first use, released by rklt_destroy; destroy a plan only after the
+ * work that uses it has finished); when the slots run out the grouped form is used.
+ * The device buffers named in h_items and d_sse / d_psnr are baked into the graph:
+ * refill them between runs, keep them alive until rklt_batch_destroy.
  * Errors: as rklt_fused_items. */
 rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *const *plans, int nplans,
                               double *d_sse, float *d_psnr, int flags, rklt_batch **out);
@@ -271,8 +283,17 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
 /* Replay the batch's graph on `stream`.  Errors: RKLT_ERR_ARG, RKLT_ERR_CUDA. */
 rklt_status rklt_batch_run(rklt_batch *b, void *stream);
 
-/* The shape the batch runs with; tuned_us = best timed run (0 without autotune). */
-rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us);
+/* The shape the batch runs with: mode 1 = one persistent queue launch, 0 = grouped
+ * launches (groups = the number of (plan, support) groups); tuned_us = best timed
+ * run (0 without autotune).  Any output pointer may be NULL. */
+rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us,
+                            int *mode);
+
+/* The autotuner's timings: for k < min(*count, max_out), candidate k's mode (as
+ * rklt_batch_info), threads per CTA, CTAs per SM and time per run in microseconds.
+ * *count = number of candidates timed.  Errors: RKLT_ERR_ARG. */
+rklt_status rklt_batch_candidates(const rklt_batch *b, int *modes, int *threads, int *ctas_per_sm, double *us,
+                                  int max_out, int *count);
 
 /* Wait for the batch's own stream, free its device memory and graph (NULL ignored). */
 void rklt_batch_destroy(rklt_batch *b);

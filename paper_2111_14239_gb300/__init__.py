@@ -95,7 +95,8 @@ _SIGS = {
     "rklt_fused_items": (_I, [_P, _I, _P, _I, _P, _P, _P]),
     "rklt_batch_create": (_I, [_P, _I, _P, _I, _P, _P, _I, ctypes.POINTER(_P)]),
     "rklt_batch_run": (_I, [_P, _P]),
-    "rklt_batch_info": (_I, [_P, _P, _P, _P, _P]),
+    "rklt_batch_info": (_I, [_P, _P, _P, _P, _P, _P]),
+    "rklt_batch_candidates": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "rklt_batch_destroy": (None, [_P]),
     "rklt_rsweep": (_I, [_P, _I, _P, _I, _I, _I, _L, _L, _P, _P, _P]),
     "rklt_server_create": (_I, [_P, _I, ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
@@ -385,9 +386,16 @@ class Batch:
         _check(lib.rklt_batch_run(self._h, _stream(stream)))
 
     def info(self):
-        t, c, g, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        _check(lib.rklt_batch_info(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g), ctypes.byref(us)))
-        return {"threads": t.value, "ctas_per_sm": c.value, "groups": g.value, "tuned_us": us.value}
+        t, c, g, us, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(lib.rklt_batch_info(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g), ctypes.byref(us),
+                                   ctypes.byref(m)))
+        n = ctypes.c_int()
+        md, th, cs, ts = (ctypes.c_int * 16)(), (ctypes.c_int * 16)(), (ctypes.c_int * 16)(), (ctypes.c_double * 16)()
+        _check(lib.rklt_batch_candidates(self._h, md, th, cs, ts, 16, ctypes.byref(n)))
+        cands = [{"mode": "queue" if md[k] else "grouped", "threads": th[k], "ctas_per_sm": cs[k],
+                  "us": round(ts[k], 1)} for k in range(min(n.value, 16))]
+        return {"mode": "one queue launch" if m.value else "grouped launches", "threads": t.value,
+                "ctas_per_sm": c.value, "groups": g.value, "tuned_us": us.value, "candidates": cands}
 
     def matrix(self):
         """The analysis matrix (float64 [N,N]): T-hat = S T, or the exact KLT / DCT."""

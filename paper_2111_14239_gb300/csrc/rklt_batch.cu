@@ -34,6 +34,8 @@ struct BatchItem {
     int bw, units_x;    // blocks per block-row, units per block-row
     int vec4;           // coefficients as float4 (r % 4 == 0, 16-byte aligned)
     int out_index;      // position of this item in the caller's d_sse / d_psnr
+    int slot;           // the plan's slot in the constant-memory plan table (queue kernel)
+    int64_t nunits;     // units of this item
 };
 
 // Last item whose unit range starts at or before u, searching forward from lo
@@ -139,31 +141,180 @@ __global__ void __launch_bounds__(256, 1)
     cp_async_wait<0>();
 }
 
-// One CTA per item: FP64 sum of its unit partials in order, then PSNR.
-__global__ void batch_finalize(const BatchItem *__restrict__ items, int nitems, int64_t nunits,
-                               const float *__restrict__ partials, double *sse, float *psnr) {
-    __shared__ double red[256];
-    const int i = blockIdx.x;
-    if (i >= nitems) return;
-    const BatchItem it = items[i];
-    const int64_t end = (i + 1 < nitems) ? items[i + 1].unit_base : nunits;
+// Sum of an item's unit partials by one warp, in a fixed order (lane-strided
+// FP64 sums, then a fixed shuffle tree), then SSE and PSNR.
+__device__ __forceinline__ void finalize_item(const BatchItem &it, const float *partials, double *sse, float *psnr,
+                                              int lane) {
     double acc = 0.0;
-    for (int64_t u = it.unit_base + threadIdx.x; u < end; u += blockDim.x) acc += double(partials[u]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double s = red[0], npx = double(it.H) * double(it.W);
-        sse[it.out_index] = s;
+    for (int64_t u = it.unit_base + lane; u < it.unit_base + it.nunits; u += 32)
+        acc += double(__ldcg(partials + u));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        const double npx = double(it.H) * double(it.W);
+        sse[it.out_index] = acc;
         float p;
         if (npx == 0.0) p = __int_as_float(0x7fc00000);
-        else if (s == 0.0) p = __int_as_float(0x7f800000);
-        else p = float(10.0 * log10(255.0 * 255.0 * npx / s));
+        else if (acc == 0.0) p = __int_as_float(0x7f800000);
+        else p = float(10.0 * log10(255.0 * 255.0 * npx / acc));
         psnr[it.out_index] = p;
     }
+}
+
+// One warp per item (grouped launches): the same sum as the queue kernel's, so
+// both forms give bit-identical results.
+__global__ void batch_finalize(const BatchItem *__restrict__ items, int nitems, int64_t nunits,
+                               const float *__restrict__ partials, double *sse, float *psnr) {
+    const int i = blockIdx.x;
+    if (i >= nitems) return;
+    finalize_item(items[i], partials, sse, psnr, int(threadIdx.x));
+}
+
+// ---------------------------------------------------------------------------
+// One persistent launch for a whole batch (all plans, all diagonal bounds).
+// Plans live in a constant-memory table (one slot per plan and device, written once
+// before first use); each unit dispatches on its item's D; the warp that completes
+// an item's last unit sums the item's unit partials in order and writes its SSE and
+// PSNR, then clears the item's counter for the next run.  Units are queued heaviest
+// first (larger D) and dealt round-robin to the warps.
+// ---------------------------------------------------------------------------
+constexpr int kPlanSlots = 16;
+__constant__ PlanK<8> c_plans8[kPlanSlots];
+__constant__ PlanK<4> c_plans4[kPlanSlots];
+
+template <int N>
+__device__ __forceinline__ const PlanK<N> &plan_slot(int k) {
+    if constexpr (N == 8) return c_plans8[k];
+    else return c_plans4[k];
+}
+
+// The per-block computation for one diagonal bound, out of line: the queue kernel
+// calls the variant of each unit's D (each variant is compiled once, and the kernel
+// stays a small dispatcher).  src: the staged block, row stride 32 N bytes.
+template <int N, int D>
+__device__ __noinline__ float block_d(int slot, const uint8_t *src, uint8_t *dst, int64_t ldd, int r, float *coef,
+                                      bool vec4, bool recon) {
+    uint32_t w[N][N / 4];
+    load_block_words<N>(src, 32 * N, w);
+    return block_core<N, D>(plan_slot<N>(slot), w, dst, ldd, r, coef, vec4, recon);
+}
+
+template <int N, int D = 0>
+__device__ __forceinline__ float block_any_d(int slot, int Dr, const uint8_t *src, uint8_t *dst, int64_t ldd, int r,
+                                             float *coef, bool vec4, bool recon) {
+    if constexpr (D >= 2 * N - 1) {
+        return block_d<N, 2 * N - 1>(slot, src, dst, ldd, r, coef, vec4, recon);
+    } else {
+        if (Dr == D) return block_d<N, D>(slot, src, dst, ldd, r, coef, vec4, recon);
+        return block_any_d<N, D + 1>(slot, Dr, src, dst, ldd, r, coef, vec4, recon);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 1)
+    queue_kernel(const BatchItem *__restrict__ items, int nitems, int64_t nunits, float *__restrict__ partials,
+                 unsigned int *__restrict__ done, double *sse, float *psnr) {
+    extern __shared__ __align__(16) uint8_t bsm[];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    if (warp0 >= nunits) return;
+    uint8_t *mine = bsm + int(threadIdx.x >> 5) * (2 * 32 * N * N) + lane * N;
+    int lo = item_of(items, nitems, 0, warp0);
+    BatchItem it = items[lo];
+    int by = 0, bx = 0;
+    bool have = unit_block(it, warp0, lane, by, bx);
+    if (have) stage_block<N>(it, by, bx, mine);
+    cp_async_commit();
+    int slot = 0;
+    for (int64_t u = warp0; u < nunits; u += nwarps) {
+        const int64_t un = u + nwarps;
+        int lon = lo, byn = 0, bxn = 0;
+        bool haven = false;
+        BatchItem itn = it;
+        if (un < nunits) {
+            lon = item_of(items, nitems, lo, un);
+            if (lon != lo) itn = items[lon];
+            haven = unit_block(itn, un, lane, byn, bxn);
+            if (haven) stage_block<N>(itn, byn, bxn, mine + (slot ^ 1) * 32 * N * N);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        float e = 0.0f;
+        if (have) {
+            uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
+            float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
+            e = block_any_d<N>(it.slot, it.D, mine + slot * 32 * N * N, dst, it.ld_recon, it.r, coef, it.vec4 != 0,
+                               dst != nullptr);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        unsigned int prev = 0;
+        if (lane == 0) {
+            partials[u] = e;
+            __threadfence();  // the partial is visible before the unit counts as done
+            prev = atomicAdd(done + lo, 1u);
+        }
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev + 1 == unsigned(it.nunits)) {  // this warp finished the item's last unit
+            __threadfence();
+            finalize_item(it, partials, sse, psnr, lane);
+            if (lane == 0) done[lo] = 0u;   // ready for the next run of the same batch
+        }
+        slot ^= 1;
+        have = haven;
+        by = byn;
+        bx = bxn;
+        lo = lon;
+        it = itn;
+    }
+    cp_async_wait<0>();
+}
+
+namespace {
+
+// Constant-memory plan table: one slot per (device, plan), written once (on a
+// private stream, so no other stream waits) before the plan's first queued use and
+// released when the plan is destroyed.
+struct Registry {
+    const Plan *slot_plan[kPlanSlots] = {};
+};
+std::mutex g_reg_mu;
+Registry g_reg[64][2];   // [device][N == 8]
+
+// Slot of `p` on the current device, writing it if new; -1 when every slot is taken.
+int plan_slot_for(const Plan &p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    Registry &R = g_reg[dev][p.N == 8 ? 1 : 0];
+    int free_k = -1;
+    for (int k = 0; k < kPlanSlots; k++) {
+        if (R.slot_plan[k] == &p) return k;
+        if (!R.slot_plan[k] && free_k < 0) free_k = k;
+    }
+    if (free_k < 0) return -1;
+    static cudaStream_t up[64] = {};
+    if (!up[dev] && cudaStreamCreateWithFlags(&up[dev], cudaStreamNonBlocking) != cudaSuccess) return -1;
+    const size_t bytes = p.N == 8 ? sizeof(PlanK<8>) : sizeof(PlanK<4>);
+    const size_t off = size_t(free_k) * bytes;
+    const cudaError_t e = p.N == 8 ? cudaMemcpyToSymbolAsync(c_plans8, p.k.data(), bytes, off,
+                                                              cudaMemcpyHostToDevice, up[dev])
+                                   : cudaMemcpyToSymbolAsync(c_plans4, p.k.data(), bytes, off,
+                                                              cudaMemcpyHostToDevice, up[dev]);
+    if (e != cudaSuccess || cudaStreamSynchronize(up[dev]) != cudaSuccess) return -1;
+    R.slot_plan[free_k] = &p;
+    return free_k;
+}
+
+}  // namespace
+
+void plan_registry_release(const Plan *p) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    for (auto &dev : g_reg)
+        for (auto &R : dev)
+            for (auto &sp : R.slot_plan)
+                if (sp == p) sp = nullptr;
 }
 
 namespace {
@@ -232,7 +383,8 @@ rklt_status build_groups(const rklt_item *h, int n, const rklt_plan *const *plan
         b.vec4 = (x.r % 4 == 0) && ((reinterpret_cast<uintptr_t>(x.d_zcoef) & 15) == 0);
         b.out_index = i;
         b.unit_base = g.nunits;
-        g.nunits += int64_t(x.H / N) * b.units_x;
+        b.nunits = int64_t(x.H / N) * b.units_x;
+        g.nunits += b.nunits;
         g.items.push_back(b);
     }
     return RKLT_OK;
@@ -267,7 +419,7 @@ cudaError_t launch_group(int N, const Group &g, const BatchItem *d_items, float 
         const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, batch_smem(N, threads), st);
         if (e != cudaSuccess) return e;
     }
-    batch_finalize<<<nitems, 256, 0, st>>>(d_items, nitems, nunits, partials, sse, psnr);
+    batch_finalize<<<nitems, 32, 0, st>>>(d_items, nitems, nunits, partials, sse, psnr);
     return cudaGetLastError();
 }
 
@@ -281,6 +433,70 @@ int grid_for(int N, int threads, int per_sm, int64_t nunits) {
     const int64_t warps_needed = nunits;
     const int64_t ctas_needed = (warps_needed * 32 + threads - 1) / threads;
     return int(std::max<int64_t>(1, std::min<int64_t>(int64_t(use) * sm_count(dev), ctas_needed)));
+}
+
+// One queue over every group: groups ordered by D (heaviest first), then plan;
+// unit bases run over the whole queue; each item carries its plan's constant slot.
+// Items without units (empty images) go to `empty`.  False if a plan gets no slot.
+bool build_queue(const std::vector<Group> &groups, std::vector<BatchItem> &q, std::vector<BatchItem> &empty,
+                 int64_t &nunits) {
+    std::vector<size_t> order(groups.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return groups[a].D > groups[b].D; });
+    q.clear();
+    empty.clear();
+    nunits = 0;
+    for (size_t gi : order) {
+        const int slot = plan_slot_for(*groups[gi].plan);
+        if (slot < 0) return false;
+        for (BatchItem b : groups[gi].items) {
+            b.slot = slot;
+            if (b.nunits == 0) {
+                b.unit_base = 0;
+                empty.push_back(b);
+                continue;
+            }
+            b.unit_base = nunits;
+            nunits += b.nunits;
+            q.push_back(b);
+        }
+    }
+    return true;
+}
+
+const void *queue_kernel_for(int N) {
+    return N == 8 ? reinterpret_cast<const void *>(queue_kernel<8>) : reinterpret_cast<const void *>(queue_kernel<4>);
+}
+
+int queue_grid(int N, int threads, int per_sm, int64_t nunits) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int occ = occupancy(queue_kernel_for(N), threads, batch_smem(N, threads));
+    const int use = std::max(1, std::min(per_sm, occ));
+    const int64_t ctas_needed = (nunits * 32 + threads - 1) / threads;
+    return int(std::max<int64_t>(1, std::min<int64_t>(int64_t(use) * sm_count(dev), ctas_needed)));
+}
+
+// Empty items (H or W = 0): SSE 0, PSNR NaN.
+__global__ void empty_items(const BatchItem *__restrict__ items, int n, double *sse, float *psnr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sse[items[i].out_index] = 0.0;
+    psnr[items[i].out_index] = __int_as_float(0x7fc00000);
+}
+
+cudaError_t launch_queue(int N, const BatchItem *d_items, int nitems, int64_t nunits, const BatchItem *d_empty,
+                         int nempty, float *partials, unsigned int *done, double *sse, float *psnr, int threads,
+                         int per_sm, cudaStream_t st) {
+    if (nunits > 0) {
+        const int grid = queue_grid(N, threads, per_sm, nunits);
+        void *args[] = {&d_items, &nitems, &nunits, &partials, &done, &sse, &psnr};
+        const cudaError_t e =
+            cudaLaunchKernel(queue_kernel_for(N), dim3(grid), dim3(threads), args, batch_smem(N, threads), st);
+        if (e != cudaSuccess) return e;
+    }
+    if (nempty > 0) empty_items<<<(nempty + 127) / 128, 128, 0, st>>>(d_empty, nempty, sse, psnr);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -303,6 +519,18 @@ struct rklt_batch {
     std::vector<cudaEvent_t> join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // one persistent launch over the whole queue (mode 1)
+    int mode = 0;                      // 0 grouped launches, 1 queue kernel
+    struct Timed {
+        int mode, threads, per_sm;
+        double us;
+    };
+    std::vector<Timed> tuned;          // every candidate the autotuner timed
+    int64_t q_units = 0;
+    int q_items = 0, q_empty = 0;
+    rklt::BatchItem *dq_items = nullptr, *dq_empty = nullptr;
+    float *dq_partials = nullptr;
+    unsigned int *dq_done = nullptr;
 };
 
 using namespace rklt;
@@ -315,6 +543,10 @@ void batch_free(rklt_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto p : b->d_items) cudaFree(p);
     for (auto p : b->d_partials) cudaFree(p);
+    cudaFree(b->dq_items);
+    cudaFree(b->dq_empty);
+    cudaFree(b->dq_partials);
+    cudaFree(b->dq_done);
     if (b->stream) cudaStreamDestroy(b->stream);
     for (auto s : b->side) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
@@ -324,9 +556,19 @@ void batch_free(rklt_batch *b) {
 
 constexpr int kBatchSideStreams = 4;
 
+cudaError_t batch_enqueue_groups(rklt_batch *b, int threads, int per_sm, cudaStream_t st);
+
+// One run of the batch in mode 0 (grouped launches) or 1 (one queue launch).
+cudaError_t batch_enqueue(rklt_batch *b, int mode, int threads, int per_sm, cudaStream_t st) {
+    if (mode == 1)
+        return launch_queue(b->N, b->dq_items, b->q_items, b->q_units, b->dq_empty, b->q_empty, b->dq_partials,
+                            b->dq_done, b->sse, b->psnr, threads, per_sm, st);
+    return batch_enqueue_groups(b, threads, per_sm, st);
+}
+
 // Groups go round-robin over the side streams, largest first (the groups are
 // independent: each has its own items, partials and outputs).
-cudaError_t batch_enqueue(rklt_batch *b, int threads, int per_sm, cudaStream_t st) {
+cudaError_t batch_enqueue_groups(rklt_batch *b, int threads, int per_sm, cudaStream_t st) {
     const bool fan = !b->side.empty();
     cudaError_t e = cudaSuccess;
     if (fan) {
@@ -517,26 +759,56 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
         return e == cudaErrorMemoryAllocation ? fail(RKLT_ERR_OOM, "device allocation for the batch failed")
                                               : cuda_fail(e, "batch set-up");
     }
-    // autotuner: time each launch shape twice on the batch's own data and keep the fastest
+    // the whole batch as one queue for the persistent kernel (when every plan gets a
+    // constant-memory slot); its item counters start at zero and each run leaves them so
+    bool queue_ok = false;
+    if (e == cudaSuccess) {
+        std::vector<BatchItem> q, em;
+        queue_ok = build_queue(b->groups, q, em, b->q_units);
+        if (queue_ok) {
+            b->q_items = int(q.size());
+            b->q_empty = int(em.size());
+            e = cudaMalloc(&b->dq_items, std::max<size_t>(q.size(), 1) * sizeof(BatchItem));
+            if (e == cudaSuccess) e = cudaMalloc(&b->dq_empty, std::max<size_t>(em.size(), 1) * sizeof(BatchItem));
+            if (e == cudaSuccess) e = cudaMalloc(&b->dq_partials, size_t(std::max<int64_t>(b->q_units, 1)) * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&b->dq_done, std::max<size_t>(q.size(), 1) * sizeof(unsigned int));
+            if (e == cudaSuccess && !q.empty())
+                e = cudaMemcpy(b->dq_items, q.data(), q.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && !em.empty())
+                e = cudaMemcpy(b->dq_empty, em.data(), em.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemset(b->dq_done, 0, std::max<size_t>(q.size(), 1) * sizeof(unsigned int));
+        }
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch queue set-up");
+    }
+    // autotuner: time every candidate twice on the batch's own data and keep the
+    // fastest.  Candidates: one persistent queue launch (threads per CTA x CTAs per
+    // SM) and the grouped launches fanned over side streams (the same shapes).
     struct Cand {
-        int threads, per_sm;
+        int mode, threads, per_sm;
     };
-    std::vector<Cand> cands = {{256, 1}, {128, 2}, {128, 1}, {256, 2}};
+    std::vector<Cand> cands = {{0, 256, 1}, {0, 128, 2}, {0, 128, 1}, {0, 256, 2}};
+    if (queue_ok) cands.insert(cands.end(), {{1, 256, 1}, {1, 128, 2}, {1, 128, 1}});
     if (!(flags & 1)) cands.resize(1);
     double best = 1e30;
+    b->tuned.clear();
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (const Cand &c : cands) {
-        if (batch_enqueue(b, c.threads, c.per_sm, b->stream) != cudaSuccess) continue;  // warm-up
+        if (batch_enqueue(b, c.mode, c.threads, c.per_sm, b->stream) != cudaSuccess) continue;  // warm-up
         cudaEventRecord(e0, b->stream);
-        for (int rep = 0; rep < 2; rep++) batch_enqueue(b, c.threads, c.per_sm, b->stream);
+        for (int rep = 0; rep < 2; rep++) batch_enqueue(b, c.mode, c.threads, c.per_sm, b->stream);
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) continue;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
+        b->tuned.push_back({c.mode, c.threads, c.per_sm, ms / 2 * 1e3});
         if (ms / 2 < best) {
             best = ms / 2;
+            b->mode = c.mode;
             b->threads = c.threads;
             b->per_sm = c.per_sm;
         }
@@ -547,7 +819,7 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
     // capture the chosen launch sequence once; runs replay the graph
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const cudaError_t le = batch_enqueue(b, b->threads, b->per_sm, b->stream);
+        const cudaError_t le = batch_enqueue(b, b->mode, b->threads, b->per_sm, b->stream);
         e = cudaStreamEndCapture(b->stream, &b->graph);
         if (le != cudaSuccess) e = le;
     }
@@ -567,12 +839,27 @@ rklt_status rklt_batch_run(rklt_batch *b, void *stream) {
     return e == cudaSuccess ? RKLT_OK : cuda_fail(e, "graph launch");
 }
 
-rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us) {
+rklt_status rklt_batch_info(const rklt_batch *b, int *threads, int *ctas_per_sm, int *groups, double *tuned_us,
+                            int *mode) {
     if (!b) return fail(RKLT_ERR_ARG, "batch is NULL");
     if (threads) *threads = b->threads;
     if (ctas_per_sm) *ctas_per_sm = b->per_sm;
     if (groups) *groups = int(b->groups.size());
     if (tuned_us) *tuned_us = b->tuned_us;
+    if (mode) *mode = b->mode;
+    return RKLT_OK;
+}
+
+rklt_status rklt_batch_candidates(const rklt_batch *b, int *modes, int *threads, int *ctas_per_sm, double *us,
+                                  int max_out, int *count) {
+    if (!b || !count) return fail(RKLT_ERR_ARG, "batch and count are required");
+    *count = int(b->tuned.size());
+    for (int k = 0; k < *count && k < max_out; k++) {
+        if (modes) modes[k] = b->tuned[size_t(k)].mode;
+        if (threads) threads[k] = b->tuned[size_t(k)].threads;
+        if (ctas_per_sm) ctas_per_sm[k] = b->tuned[size_t(k)].per_sm;
+        if (us) us[k] = b->tuned[size_t(k)].us;
+    }
     return RKLT_OK;
 }
 

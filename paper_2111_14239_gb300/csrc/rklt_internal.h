@@ -156,6 +156,9 @@ inline bool uses_tmem_kernel(const Plan &p, int D, int engine) {
 }
 inline int fused_tile_rows(const Plan &p, int D, int engine) { return uses_tmem_kernel(p, D, engine) ? 32 : kTileH; }
 
+// Frees the constant-memory plan slots the batch kernels gave `p` (rklt_batch.cu).
+void plan_registry_release(const Plan *p);
+
 // Device wait timeout (nanoseconds) for the next launches.
 uint64_t wait_timeout_ns();
 

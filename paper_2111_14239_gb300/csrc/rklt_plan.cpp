@@ -447,7 +447,10 @@ rklt_status rklt_plan_matrix(const rklt_plan *plan, double *h_M) {
     return RKLT_OK;
 }
 
-void rklt_destroy(rklt_plan *plan) { delete plan; }
+void rklt_destroy(rklt_plan *plan) {
+    if (plan) rklt::plan_registry_release(&plan->p);
+    delete plan;
+}
 
 rklt_status rklt_plan_info(const rklt_plan *plan, int8_t *h_T, double *h_s, int *orthogonal,
                            int *N_out, double *alpha_out, double *rho_out) {
