@@ -249,6 +249,23 @@ __device__ __forceinline__ uint32_t bytes4_biased(float v0, float v1, float v2, 
     return __byte_perm(h01, h23, 0x6420);
 }
 
+// Sum of the four signed byte products a_k b_k (a signed, b unsigned) plus c.
+__device__ __forceinline__ int dp4a_su(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// 4 x 4 byte transpose: out[c] holds byte c of r0, r1, r2, r3 (in that order).
+__device__ __forceinline__ void transpose4x4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t (&out)[4]) {
+    const uint32_t x0 = __byte_perm(r0, r1, 0x5140), x1 = __byte_perm(r0, r1, 0x7362);
+    const uint32_t x2 = __byte_perm(r2, r3, 0x5140), x3 = __byte_perm(r2, r3, 0x7362);
+    out[0] = __byte_perm(x0, x2, 0x5410);
+    out[1] = __byte_perm(x0, x2, 0x7632);
+    out[2] = __byte_perm(x1, x3, 0x5410);
+    out[3] = __byte_perm(x1, x3, 0x7632);
+}
+
 // clip(floor(x + 1/2), 0, 255): round-half-up then saturate to 8 bits.
 __device__ __forceinline__ uint32_t recon_byte(float x) {
     float v = fminf(fmaxf(x + 0.5f, 0.0f), 255.0f);

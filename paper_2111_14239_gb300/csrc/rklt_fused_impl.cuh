@@ -74,12 +74,10 @@ __device__ __forceinline__ float quant_code(const PlanK<N> &P, int i, int j, flo
 // ---------------------------------------------------------------------------
 // Register path: one N x N block per thread.  D is a compile-time constant.
 //
-// The column pass runs on packed binary16 pairs (two columns per instruction):
-// pixels, their mirrored sums (<= 510) and differences, and every partial sum of
-// T A (|.| <= N * 255 <= 2040) are integers below 2048, which binary16 represents
-// exactly, so the pass is still exact.  The row pass, the inverse and the error
-// run in FP32; the error takes each pixel straight from its exact half with a
-// mixed-precision subtraction.
+// The column pass runs as byte dot products (dp4a) on the transposed block: T's
+// rows as packed signed bytes against four pixels of one column, exact in int32.
+// The row pass, the inverse and the error run in FP32; the error takes each pixel
+// straight from its exact binary16 form with a mixed-precision subtraction.
 // ---------------------------------------------------------------------------
 // Loads the N x N block at src (row stride ld bytes) as N/4 words per row.
 template <int N>
@@ -149,24 +147,26 @@ __device__ __forceinline__ float block_core(const PlanK<N> &P, const uint32_t (&
             }
         }
     } else {
-    #pragma unroll
-        for (int p = 0; p < NP; p++) {
-            __half2 sp[H2], dp[H2];
-    #pragma unroll
-            for (int j = 0; j < H2; j++) {
-                const __half2 top = px(j, p), bot = px(N - 1 - j, p);
-                sp[j] = __hadd2(top, bot);
-                dp[j] = __hsub2(top, bot);
+        // byte dot products on the transposed block (T as signed bytes): exact int32
+        uint32_t tw[N][N / 4];   // [column][row group]
+#pragma unroll
+        for (int h = 0; h < N / 4; h++)
+#pragma unroll
+            for (int q = 0; q < N / 4; q++) {
+                uint32_t o[4];
+                transpose4x4(w[4 * h][q], w[4 * h + 1][q], w[4 * h + 2][q], w[4 * h + 3][q], o);
+#pragma unroll
+                for (int c = 0; c < 4; c++) tw[4 * q + c][h] = o[c];
             }
-    #pragma unroll
-            for (int i = 0; i < DR; i++) {
-                __half2 acc = __hmul2(as_h2(P.T2[i][0]), (i & 1) ? dp[0] : sp[0]);
-    #pragma unroll
-                for (int j = 1; j < H2; j++) acc = __hfma2(as_h2(P.T2[i][j]), (i & 1) ? dp[j] : sp[j], acc);
-                Y[i][2 * p] = __low2float(acc);
-                Y[i][2 * p + 1] = __high2float(acc);
+#pragma unroll
+        for (int i = 0; i < DR; i++)
+#pragma unroll
+            for (int c = 0; c < N; c++) {
+                int y = 0;
+#pragma unroll
+                for (int h = 0; h < N / 4; h++) y = dp4a_su(P.T8[i][h], tw[c][h], y);
+                Y[i][c] = float(y);
             }
-        }
     }
     // row transform: C = Y T^T on the support i + j < D; zonal mask on the last diagonal
     // (quantised: only Bq = Bbar is kept, as exact FP32 integers; the inverse forms

@@ -30,6 +30,7 @@ struct PlanK {
     static constexpr int RN = N <= 8 ? N : 2;
     float2 Td[RN][RN / 2];
     float2 Tid[RN / 2][RN];
+    uint32_t T8[RN][RN / 4];     // T[i][4h .. 4h+3] as packed signed bytes (byte dot products)
     float T[N][N / 2];    // T[i][j], j < N/2           (entries 0, +1, -1)
     alignas(8) float Ti[N / 2][N];   // T^{-1}[l][j], l < N/2 (inverse of the bare integer T); pairs
                                      // (Ti[l][2m], Ti[l][2m+1]) are 8-byte aligned

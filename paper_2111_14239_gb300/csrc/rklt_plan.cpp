@@ -126,6 +126,13 @@ void fill_kparams(Plan &p) {
             for (int l = 0; l < M / 2; l++) k.Td[j][l] = make_float2(k.T[j][l], k.T[j][l]);
         for (int c = 0; c < M / 2; c++)
             for (int j = 0; j < M; j++) k.Tid[c][j] = make_float2(k.Ti[c][j], k.Ti[c][j]);
+        if (p.kind == 0)
+            for (int i = 0; i < M; i++)
+                for (int h = 0; h < M / 4; h++) {
+                    uint32_t v = 0;
+                    for (int q = 0; q < 4; q++) v |= uint32_t(uint8_t(int8_t(p.T[size_t(i) * M + 4 * h + q]))) << (8 * q);
+                    k.T8[i][h] = v;
+                }
     }
     for (int i = 0; i < M; i++)
         for (int j = 0; j < M; j++) k.sij[i][j] = float(p.s[i] * p.s[j]);

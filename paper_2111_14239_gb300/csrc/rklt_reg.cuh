@@ -4,7 +4,7 @@
 // integers.  Included by rklt_reg_n4.cu and rklt_reg_n8.cu.
 //
 // Per block (Sec. 4.1 and the Appendix of arXiv 2111.14239):
-//   C  = T A T^T                 exact (binary16 column pass, FP32 row pass)
+//   C  = T A T^T                 exact (int32 byte-dot-product column pass, FP32 row pass)
 //   B  = (s s^T) o C             first r zig-zag coefficients (Eq. 1, Sec. 4.1)
 //   A' = T^{-1} (M o C) T^{-T}   8-bit output clip(floor(A' + 1/2), 0, 255)
 //   SSE of the block = sum a^2 - sum_retained C_ij^2 / (d_i d_j),  d = diag(T T^T)
@@ -14,8 +14,9 @@
 // are exact 64-bit integer sums (order-free: identical alone, in a batch, in any
 // grid) and the SSE is exactly that of the unrounded reconstruction A'.
 //
+// Column pass: dp4a on transposed bytes, four terms per instruction, T's rows as
+// packed signed bytes (T is in {0, +1, -1}).
 // Operand pairing for the packed FP32 instructions (FADD2 / FFMA2 / FMUL2):
-//   column pass   two adjacent columns per binary16 pair (bytes come in that way)
 //   row pass      two rows (i, i+1) per pair; T's entries as (t, t) constant pairs
 //   U = T^{-1} C' two rows of C' per pair against (T^{-1}[k][i], T^{-1}[k][i+1]): the
 //                 lanes collect the even-i and odd-i sums, U[k] = e + o, U[N-1-k] = e - o
@@ -65,42 +66,32 @@ __device__ __forceinline__ uint64_t pars_blocks(const PlanK<N> &P, const uint32_
             }
     }
 
-    // ---- column pass Y = T A (rows i < DR), two columns per binary16 pair.  Pixels
-    // arrive biased as 1024 + a; top - bot and top + (bot - 2048) are the exact
-    // difference and sum of mirrored pixels, and every partial sum of Y is an integer
-    // below 2048, so the pass is exact in binary16.
-    const __half2 k2048 = __float2half2_rn(2048.0f);
+    // ---- column pass Y = T A (rows i < DR) by byte dot products: the block's columns
+    // become words of four rows (PRMT 4 x 4 transposes), and Y[i][c] = sum_k T[i][k]
+    // A[k][c] is exact in int32 (T as signed bytes, pixels unsigned); |Y| < 2^11, so
+    // the conversion to FP32 is exact
     float Y[B][DA][N];
 #pragma unroll
-    for (int p = 0; p < NP; p++) {
-        __half2 sp[B][H2], dp[B][H2];
+    for (int b = 0; b < B; b++) {
+        uint32_t tw[N][N / 4];   // [column][row group]
 #pragma unroll
-        for (int j = 0; j < H2; j++)
+        for (int h = 0; h < N / 4; h++)
 #pragma unroll
-            for (int b = 0; b < B; b++) {
-                const __half2 top = as_h2(bytes_to_biased_h2(w[b][j][p >> 1], (2 * p) & 3, (2 * p + 1) & 3));
-                const __half2 bot = as_h2(bytes_to_biased_h2(w[b][N - 1 - j][p >> 1], (2 * p) & 3, (2 * p + 1) & 3));
-                dp[b][j] = __hsub2(top, bot);
-                sp[b][j] = __hadd2(top, __hsub2(bot, k2048));
+            for (int q = 0; q < N / 4; q++) {
+                uint32_t o[4];
+                transpose4x4(w[b][4 * h][q], w[b][4 * h + 1][q], w[b][4 * h + 2][q], w[b][4 * h + 3][q], o);
+#pragma unroll
+                for (int c = 0; c < 4; c++) tw[4 * q + c][h] = o[c];
             }
 #pragma unroll
-        for (int i = 0; i < DR; i++) {
-            __half2 acc[B];
+        for (int i = 0; i < DR; i++)
 #pragma unroll
-            for (int j = 0; j < H2; j++) {
-                const __half2 t = as_h2(P.T2[i][j]);
+            for (int c = 0; c < N; c++) {
+                int y = 0;
 #pragma unroll
-                for (int b = 0; b < B; b++) {
-                    const __half2 v = (i & 1) ? dp[b][j] : sp[b][j];
-                    acc[b] = j == 0 ? __hmul2(t, v) : __hfma2(t, v, acc[b]);
-                }
+                for (int h = 0; h < N / 4; h++) y = dp4a_su(P.T8[i][h], tw[c][h], y);
+                Y[b][i][c] = float(y);
             }
-#pragma unroll
-            for (int b = 0; b < B; b++) {
-                Y[b][i][2 * p] = __low2float(acc[b]);
-                Y[b][i][2 * p + 1] = __high2float(acc[b]);
-            }
-        }
     }
 
     // ---- row pass C = Y T^T on the support i + j < D, rows in pairs (exact: integers
