@@ -592,8 +592,20 @@ def leg_mssim(rk, d_img, dev, stream):
     npos = nimg * (H - 10) * (W - 10)
     tflops = npos * 176.0 / (ms / 1e3) / 1e12
     fp32_peak, sms, mhz = fp32_peak_tflops(dev)
+    # the fused pass with MSSIM in one launch, against the fused pass + this pass
+    fused_ms = _time_ms(lambda: rk.rklt_fused_batched(plan, d_img, r, sse, ps, recon=rec, stream=stream), 10, stream)
+    ms2 = torch.empty_like(out)
+    one_rec = _time_ms(lambda: rk.rklt_fused_mssim(plan, d_img, r, sse, ps, ms2, recon=rec, stream=stream), 10,
+                       stream)
+    one_norec = _time_ms(lambda: rk.rklt_fused_mssim(plan, d_img, r, sse, ps, ms2, stream=stream), 10, stream)
+    torch.cuda.synchronize()
+    fused_vs_two = float((ms2 - out).abs().max().item())
     return {"workload": f"{nimg} x {H}x{W}: original vs 8-bit RKLT reconstruction (N=8, r=8)",
             "ms": round(ms, 4), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4),
+            "fused_then_mssim_ms": round(fused_ms + ms, 4),
+            "fused_mssim_one_launch_ms": round(one_rec, 4),
+            "fused_mssim_one_launch_no_recon_ms": round(one_norec, 4),
+            "one_launch_vs_two_pass_max_abs_mssim_diff": fused_vs_two,
             "roofline": {"bound": "alu", "achieved": round(tflops, 2), "peak": round(fp32_peak, 1),
                          "unit": "TFLOP/s", "frac": round(tflops / fp32_peak, 4),
                          "flop_per_position": 176,

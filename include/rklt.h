@@ -406,6 +406,25 @@ rklt_status rklt_fused_quant(const rklt_plan *plan, const uint8_t *d_img, int ni
 rklt_status rklt_mssim(const uint8_t *d_x, const uint8_t *d_y, int nimg, int H, int W, int64_t ldx,
                        int64_t x_stride, int64_t ldy, int64_t y_stride, double *d_mssim, void *stream);
 
+/* rklt_fused_batched and rklt_mssim in one pass (Sec. 4.1: PSNR and SSIM of the
+ * reconstruction): the fused pass's outputs (d_zcoef, d_recon optional; d_sse,
+ * d_psnr required) plus d_mssim[nimg] (FP64), the MSSIM of each original against its
+ * 8-bit reconstruction, computed while the reconstruction is in shared memory, so
+ * d_recon may be NULL and the reconstruction never reaches HBM.  Arguments and
+ * layouts as rklt_fused_batched; d_mssim device memory.
+ * One launch for the register-path plans: N = 4, or N = 8 with r <= 15, T T^T
+ * diagonal (the rounded plans of the paper for rho < 0.39 or >= 0.8).  There the
+ * coefficients, reconstruction, SSE and PSNR are bit-identical to rklt_fused_batched,
+ * the SSIM at every window position bit-identical to rklt_mssim's on that
+ * reconstruction, and the mean differs from rklt_mssim's only in the grouping of its
+ * FP32 partial sums (about 1e-7).  Other plans run rklt_fused_batched and then
+ * rklt_mssim (with a stream-ordered scratch reconstruction when d_recon is NULL).
+ * NaN MSSIM when H or W < 11.  The result does not depend on nimg.
+ * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_OOM, RKLT_ERR_CUDA. */
+rklt_status rklt_fused_mssim(const rklt_plan *plan, const uint8_t *d_img, int nimg, int H, int W, int64_t ld,
+                             int64_t img_stride, int r, float *d_zcoef, uint8_t *d_recon, int64_t ld_recon,
+                             int64_t recon_stride, double *d_sse, float *d_psnr, double *d_mssim, void *stream);
+
 /* rklt_fused for callers that must not allocate.  (Not part of the paper: this
  * is a deployment variant of the fused pass, with no counterpart in the method.)
  *

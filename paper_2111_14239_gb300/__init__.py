@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "RklTError", "Plan", "lib", "header_symbols", "rklt_make", "rklt_make_alpha", "rklt_make_from_matrix",
     "rklt_make_klt", "rklt_make_dct", "rklt_design_sweep", "rklt_figures", "rklt_plan_info", "rklt_forward_int", "rklt_forward", "rklt_zonal", "rklt_inverse", "rklt_psnr",
-    "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_mssim", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
+    "rklt_fused", "rklt_fused_batched", "rklt_fused_quant", "rklt_mssim", "rklt_fused_mssim", "rklt_fused_noalloc", "rklt_device_status", "RklTItem", "make_items",
     "rklt_fused_items", "Batch", "rklt_batch_create", "rklt_rsweep", "rklt_set_wait_timeout_us",
     "rklt_set_transport", "rklt_set_tensor_engine", "rklt_debug_inject_stall", "rklt_version", "default_alpha", "nblocks",
     "RklTRequest", "RklTResult", "NativeServer", "rklt_server_create",
@@ -90,6 +90,7 @@ _SIGS = {
     "rklt_fused_batched": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P]),
     "rklt_fused_quant": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _P, _L, _L, _P, _P, _P]),
     "rklt_mssim": (_I, [_P, _P, _I, _I, _I, _L, _L, _L, _L, _P, _P]),
+    "rklt_fused_mssim": (_I, [_P, _P, _I, _I, _I, _L, _L, _I, _P, _P, _L, _L, _P, _P, _P, _P]),
     "rklt_fused_noalloc": (_I, [_P, _P, _I, _I, _L, _I, _P, _P, _L, _P, _P, _P]),
     "rklt_device_status": (_I, []),
     "rklt_fused_items": (_I, [_P, _I, _P, _I, _P, _P, _P]),
@@ -326,6 +327,20 @@ def rklt_fused_quant(plan: Plan, imgs, r: int, Q, sse, psnr, qcoef=None, recon=N
     ldr, rstr = (recon.stride(1), recon.stride(0)) if recon is not None else (0, 0)
     _check(lib.rklt_fused_quant(plan.handle, imgs.data_ptr(), nimg, H, W, imgs.stride(1), imgs.stride(0), r,
                                 Qh.ctypes.data, _ptr(qcoef), _ptr(recon), ldr, rstr, _ptr(sse), _ptr(psnr),
+                                _stream(stream)))
+
+
+def rklt_fused_mssim(plan: Plan, imgs, r: int, sse, psnr, mssim, zcoef=None, recon=None, stream=None):
+    """rklt_fused_batched plus the MSSIM of each image against its reconstruction, in
+    one pass.  imgs: uint8 [H, W] or [nimg, H, W]; mssim: float64 [nimg]."""
+    if imgs.dim() == 2:
+        imgs = imgs.unsqueeze(0)
+        recon = recon.unsqueeze(0) if recon is not None else None
+    assert imgs.dim() == 3 and imgs.stride(2) == 1
+    nimg, H, W = imgs.shape
+    ldr, rstr = (recon.stride(1), recon.stride(0)) if recon is not None else (0, 0)
+    _check(lib.rklt_fused_mssim(plan.handle, imgs.data_ptr(), nimg, H, W, imgs.stride(1), imgs.stride(0), r,
+                                _ptr(zcoef), _ptr(recon), ldr, rstr, _ptr(sse), _ptr(psnr), _ptr(mssim),
                                 _stream(stream)))
 
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = [
     "rklt_fused_n8.cu", "rklt_fused_n32.cu", "rklt_fused_n16.cu", "rklt_fused_n4.cu", "rklt_reg_n8.cu",
-    "rklt_reg_n8b.cu", "rklt_reg_n4.cu",
+    "rklt_reg_n8b.cu", "rklt_reg_n4.cu", "rklt_fmssim_n8.cu", "rklt_fmssim_n4.cu",
     "rklt_batch.cu", "rklt_sweep.cu", "rklt_split.cu", "rklt_noalloc.cu", "rklt_quant.cu", "rklt_mssim.cu",
     "rklt_plan.cpp", "rklt_serve.cpp",
     "rklt_host.cpp", "rklt_capi.cpp",

@@ -72,7 +72,7 @@ rklt_status rklt_device_status(void) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     unsigned int v = take_status_n4() | take_status_n8() | take_status_n16() | take_status_n32() | take_status_split() |
                      take_status_mssim() | take_status_reg_n4() | take_status_reg_n8() |
-                     take_status_reg_n8b();
+                     take_status_reg_n8b() | take_status_fm_n4() | take_status_fm_n8();
     if (v) return fail(RKLT_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return RKLT_OK;
 }

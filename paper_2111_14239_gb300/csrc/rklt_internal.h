@@ -126,6 +126,8 @@ unsigned int take_status_reg_n4();
 unsigned int take_status_reg_n8();
 unsigned int take_status_reg_n8b();
 unsigned int take_status_mssim();
+unsigned int take_status_fm_n4();
+unsigned int take_status_fm_n8();
 
 // host helpers (rklt_host.cpp)
 rklt_status fail(rklt_status st, const std::string &msg);

@@ -41,8 +41,8 @@ __device__ __forceinline__ float2 ld_pair(const float *p) { return *reinterpret_
 // are independent.  Returns the blocks' error times m^2 as an exact integer (blocks
 // with act[b] false -- outside the image -- add nothing and store no coefficients);
 // writes the coefficients (COEF) and the 8-bit reconstruction over each block's
-// bytes at dst[b], row stride TW (RECON).
-template <int N, int D, bool COEF, bool RECON, int B>
+// bytes at dst[b], row stride LDD (RECON).
+template <int N, int D, bool COEF, bool RECON, int B, int LDD = TW>
 __device__ __forceinline__ uint64_t pars_blocks(const PlanK<N> &P, const uint32_t (&w)[B][N][N / 4],
                                                 uint8_t *const (&dst)[B], int r, float *const (&coef)[B],
                                                 const bool (&act)[B], int cvec) {
@@ -304,11 +304,11 @@ __device__ __forceinline__ uint64_t pars_blocks(const PlanK<N> &P, const uint32_
                     wb[q] = bytes4_biased(bot[b][4 * q], bot[b][4 * q + 1], bot[b][4 * q + 2], bot[b][4 * q + 3]);
                 }
                 if constexpr (N == 8) {
-                    *reinterpret_cast<uint2 *>(dst[b] + k * TW) = make_uint2(wt[0], wt[1]);
-                    *reinterpret_cast<uint2 *>(dst[b] + (N - 1 - k) * TW) = make_uint2(wb[0], wb[1]);
+                    *reinterpret_cast<uint2 *>(dst[b] + k * LDD) = make_uint2(wt[0], wt[1]);
+                    *reinterpret_cast<uint2 *>(dst[b] + (N - 1 - k) * LDD) = make_uint2(wb[0], wb[1]);
                 } else {
-                    *reinterpret_cast<uint32_t *>(dst[b] + k * TW) = wt[0];
-                    *reinterpret_cast<uint32_t *>(dst[b] + (N - 1 - k) * TW) = wb[0];
+                    *reinterpret_cast<uint32_t *>(dst[b] + k * LDD) = wt[0];
+                    *reinterpret_cast<uint32_t *>(dst[b] + (N - 1 - k) * LDD) = wb[0];
                 }
             }
         }

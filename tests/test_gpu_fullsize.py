@@ -213,3 +213,14 @@ def test_mssim_workload(rk, orc, roofline):
     m = np.mean((x.astype(np.float64) - 128) ** 2) + np.mean((y.astype(np.float64) - 128) ** 2)
     bound = 4 * 22 * 2.0 ** -24 * m / (0.03 * 255) ** 2 + 1e-6
     assert abs(float(out[0].item()) - ref) <= bound
+    # the one-launch form: the same reconstruction and scalars, MSSIM within 1e-6
+    rec2 = torch.empty_like(d)
+    s2 = torch.empty_like(s)
+    p2 = torch.empty_like(p)
+    ms2 = torch.empty_like(out)
+    rk.rklt_fused_mssim(plan, d, r, s2, p2, ms2, recon=rec2)
+    torch.cuda.synchronize()
+    rk.rklt_device_status()
+    assert torch.equal(rec, rec2) and torch.equal(s, s2) and torch.equal(p, p2)
+    assert float((ms2 - out).abs().max().item()) <= 1e-6
+    assert abs(float(ms2[0].item()) - ref) <= bound
