@@ -41,10 +41,13 @@ NIMG, SIDE = 16, 4096
 # N = 16, 32: the tensor-core variant of fused_kernel.)
 KERNEL = {4: "pars_kernel<4, 2, 3>", 8: "pars_kernel<8, 4, 3>", 16: "fused_kernel<16, 4>", 32: "fused_kernel<32, 4>"}
 TRAFFIC = {
-    # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum on one launch per
-    # kernel of the 16 x 4096^2 step (profiles/fused_kernel_launches_4096x16.md)
-    "fused_kernel<16, 4>": 268536576 + 339311872,
-    "fused_kernel<32, 4>": 268518144 + 342444544,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch per kernel of the 16 x 4096^2
+    # step, from the full ncu captures (profiles/pars_kernel_n4_n8_4096x16.md,
+    # profiles/fused_kernel_tc_n16_n32_4096x16_full.md)
+    "pars_kernel<4, 2, 3>": 268489216 + 342649088,
+    "pars_kernel<8, 4, 3>": 268519168 + 344211712,
+    "fused_kernel<16, 4>": 268546048 + 343022848,
+    "fused_kernel<32, 4>": 268663552 + 343248896,
 }
 
 
@@ -370,7 +373,7 @@ def run_ours(args):
                          ("quant_jpeg_like_4096", lambda: leg_quant(rk, d_img, dev, stream)),
                          ("mssim_4096", lambda: leg_mssim(rk, d_img, dev, stream)),
                          ("r_sweep_256x512", lambda: leg_sweep(rk, dev, stream)),
-                         ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream)),
+                         ("batch_2000_uneven", lambda: leg_batch(rk, dev, stream, args.batch_images)),
                          ("serving", lambda: leg_serve(rk, dev, args.serve_seconds))):
             if args.legs and name not in args.legs.split(","):
                 continue
@@ -720,6 +723,8 @@ def main():
     ap.add_argument("--min-timed-s", type=float, default=1.0,
                     help="lower bound on the device-timed region (passes per step scale to reach it)")
     ap.add_argument("--legs", default="", help="comma-separated subset of the extra legs (profiling runs)")
+    ap.add_argument("--batch-images", type=int, default=2000,
+                    help="images of the uneven-batch leg (fewer only for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

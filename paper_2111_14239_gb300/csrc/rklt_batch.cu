@@ -85,60 +85,134 @@ __device__ __forceinline__ void stage_block(const BatchItem &it, int by, int bx,
     for (int k = 0; k < N; k++) cp_async<N>(dst + k * 32 * N, src + k * it.ld);
 }
 
-// Each warp walks units u = warp0, warp0 + nwarps, ...; the next unit's pixels are
-// copied into the warp's other shared-memory buffer (cp.async) while the current
-// unit is transformed, so the loads of one unit overlap the arithmetic of the last.
-// Dynamic shared memory: warps x 2 slots x N rows x 32 lanes x N bytes.
+// Staging slots per warp: a warp transforms one unit while the copies of the next
+// BRING - 1 are in flight.  (Four and eight slots measured no faster on the
+// 2000-image batch than two: its kernels are bound by the per-block arithmetic at
+// high diagonal bounds, not by the copies.)
+constexpr int BRING = 2;
+
+// Walks the warp's units u = warp0, warp0 + nwarps, ... through the ring: the copy of
+// unit u + (BRING - 1) nwarps is issued into the slot just freed, then unit u (landed)
+// is handed to body(u, item index, by, bx, have, staged block of this lane).  The
+// pending units' positions form a register FIFO (shifted once per unit), so the body
+// appears once in the loop.  mine: this lane's byte in slot 0 of the warp's ring
+// (slot s at + s * 32 N N).
+template <int N, class Body>
+__device__ __forceinline__ void walk_units(const BatchItem *__restrict__ items, int nitems, int64_t nunits,
+                                           int64_t warp0, int64_t nwarps, int lane, uint8_t *mine, Body body) {
+    int idx[BRING], by[BRING], bx[BRING];   // FIFO: entry j is unit u + j nwarps
+    bool have[BRING];
+    int lo = item_of(items, nitems, 0, warp0);
+    // stages unit un into ring slot s as FIFO entry j (nothing past the queue's end);
+    // one copy group
+    const auto stage = [&](int j, int s, int64_t un) {
+        have[j] = false;
+        idx[j] = lo;
+        by[j] = bx[j] = 0;
+        if (un < nunits) {
+            lo = item_of(items, nitems, lo, un);
+            idx[j] = lo;
+            const BatchItem &it = items[lo];
+            have[j] = unit_block(it, un, lane, by[j], bx[j]);
+            if (have[j]) stage_block<N>(it, by[j], bx[j], mine + s * 32 * N * N);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < BRING - 1; j++) stage(j, j, warp0 + j * nwarps);
+    int slot = 0;   // ring slot of FIFO entry 0
+#pragma unroll 1
+    for (int64_t u = warp0; u < nunits; u += nwarps) {
+        const int last = slot == 0 ? BRING - 1 : slot - 1;
+        stage(BRING - 1, last, u + (BRING - 1) * nwarps);
+        cp_async_wait<BRING - 1>();   // unit u's group (the oldest pending) has landed
+        body(u, idx[0], by[0], bx[0], have[0], mine + slot * 32 * N * N);
+#pragma unroll
+        for (int j = 0; j + 1 < BRING; j++) {
+            idx[j] = idx[j + 1];
+            by[j] = by[j + 1];
+            bx[j] = bx[j + 1];
+            have[j] = have[j + 1];
+        }
+        slot = slot == BRING - 1 ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
+// Each warp walks units u = warp0, warp0 + nwarps, ... (walk_units): the pixels of the
+// next BRING - 1 units are copied into the warp's staging ring (cp.async) while the
+// current unit is transformed.  N = 8: the coefficients (up to 64 per block) go
+// through a per-warp shared-memory stage and leave as one contiguous run per unit
+// (warp_coef_copy8) instead of 32 strided per-lane runs.
+// Dynamic shared memory (batch_smem): warps x BRING slots x N rows x 32 lanes x N
+// bytes, then for N = 8 warps x 32 lanes x STG8_LD floats.
+template <int N>
+__device__ __forceinline__ float *coef_stage(uint8_t *bsm, int warp) {
+    if constexpr (N == 8)
+        return reinterpret_cast<float *>(bsm + (blockDim.x / 32) * BRING * 32 * N * N) + warp * 32 * STG8_LD;
+    else
+        return nullptr;
+}
+
+// The unit's coefficient destination and staging: where lane's block writes its
+// coefficients (its global run for N = 4, the warp stage for N = 8), and for N = 8
+// the copy of the warp's run to global memory afterwards (all lanes).
+template <int N>
+struct UnitCoef {
+    float *run = nullptr;     // global run of the unit's first block (N = 8)
+    float *mine = nullptr;    // where this lane's block writes
+    int nb = 0;               // blocks of the unit inside the image
+    bool vec4 = false;        // this lane's block writes float4
+    __device__ __forceinline__ UnitCoef(const BatchItem &it, int by, int bx, int lane, float *stage) {
+        if (!it.zcoef || it.r == 0) return;
+        if constexpr (N == 8) {
+            const int bx0 = bx - lane;
+            run = it.zcoef + (int64_t(by) * it.bw + bx0) * it.r;
+            mine = stage + lane * STG8_LD;
+            nb = min(32, it.bw - bx0);
+            vec4 = (it.r & 3) == 0;
+        } else {
+            mine = it.zcoef + (int64_t(by) * it.bw + bx) * it.r;
+            vec4 = it.vec4 != 0;
+        }
+    }
+    __device__ __forceinline__ void flush(const BatchItem &it, float *stage, int lane) const {
+        if constexpr (N == 8) {
+            if (!run) return;
+            __syncwarp();
+            warp_coef_copy8(run, stage, nb, it.r, it.vec4 != 0, lane);
+            __syncwarp();   // the stage is rewritten by the next unit
+        }
+    }
+};
+
 template <int N, int D>
 __global__ void __launch_bounds__(256, 1)
     batch_kernel(const __grid_constant__ PlanK<N> P, const BatchItem *__restrict__ items, int nitems, int64_t nunits,
                  float *__restrict__ partials) {
     extern __shared__ __align__(16) uint8_t bsm[];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = int(threadIdx.x >> 5);
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     if (warp0 >= nunits) return;
-    uint8_t *mine = bsm + int(threadIdx.x >> 5) * (2 * 32 * N * N) + lane * N;  // slot s at + s * 32 * N * N
-    int lo = item_of(items, nitems, 0, warp0);
-    BatchItem it = items[lo];
-    int by = 0, bx = 0;
-    bool have = unit_block(it, warp0, lane, by, bx);
-    if (have) stage_block<N>(it, by, bx, mine);
-    cp_async_commit();
-    int slot = 0;
-    for (int64_t u = warp0; u < nunits; u += nwarps) {
-        // start the next unit's copies into the other slot
-        const int64_t un = u + nwarps;
-        int lon = lo, byn = 0, bxn = 0;
-        bool haven = false;
-        BatchItem itn = it;
-        if (un < nunits) {
-            lon = item_of(items, nitems, lo, un);
-            if (lon != lo) itn = items[lon];
-            haven = unit_block(itn, un, lane, byn, bxn);
-            if (haven) stage_block<N>(itn, byn, bxn, mine + (slot ^ 1) * 32 * N * N);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();  // this unit's copies (the older group) have landed
-        float sse = 0.0f;
-        if (have) {
-            uint32_t w[N][N / 4];
-            load_block_words<N>(mine + slot * 32 * N * N, 32 * N, w);
-            uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
-            float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
-            sse = block_core<N, D>(P, w, dst, it.ld_recon, it.r, coef, it.vec4 != 0, dst != nullptr);
-        }
+    uint8_t *mine = bsm + warp * (BRING * 32 * N * N) + lane * N;
+    float *stage = coef_stage<N>(bsm, warp);
+    walk_units<N>(items, nitems, nunits, warp0, nwarps, lane, mine,
+                  [&](int64_t u, int k, int by, int bx, bool have, const uint8_t *src) {
+                      const BatchItem &it = items[k];
+                      const UnitCoef<N> uc(it, by, bx, lane, stage);
+                      float sse = 0.0f;
+                      if (have) {
+                          uint32_t w[N][N / 4];
+                          load_block_words<N>(src, 32 * N, w);
+                          uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
+                          sse = block_core<N, D>(P, w, dst, it.ld_recon, it.r, uc.mine, uc.vec4, dst != nullptr);
+                      }
+                      uc.flush(it, stage, lane);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
-        if (lane == 0) partials[u] = sse;
-        slot ^= 1;
-        have = haven;
-        by = byn;
-        bx = bxn;
-        lo = lon;
-        it = itn;
-    }
-    cp_async_wait<0>();
+                      for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
+                      if (lane == 0) partials[u] = sse;
+                  });
 }
 
 // Sum of an item's unit partials by one warp, in a fixed order (lane-strided
@@ -219,56 +293,35 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     if (warp0 >= nunits) return;
-    uint8_t *mine = bsm + int(threadIdx.x >> 5) * (2 * 32 * N * N) + lane * N;
-    int lo = item_of(items, nitems, 0, warp0);
-    BatchItem it = items[lo];
-    int by = 0, bx = 0;
-    bool have = unit_block(it, warp0, lane, by, bx);
-    if (have) stage_block<N>(it, by, bx, mine);
-    cp_async_commit();
-    int slot = 0;
-    for (int64_t u = warp0; u < nunits; u += nwarps) {
-        const int64_t un = u + nwarps;
-        int lon = lo, byn = 0, bxn = 0;
-        bool haven = false;
-        BatchItem itn = it;
-        if (un < nunits) {
-            lon = item_of(items, nitems, lo, un);
-            if (lon != lo) itn = items[lon];
-            haven = unit_block(itn, un, lane, byn, bxn);
-            if (haven) stage_block<N>(itn, byn, bxn, mine + (slot ^ 1) * 32 * N * N);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-        float e = 0.0f;
-        if (have) {
-            uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
-            float *coef = it.zcoef ? it.zcoef + (int64_t(by) * it.bw + bx) * it.r : nullptr;
-            e = block_any_d<N>(it.slot, it.D, mine + slot * 32 * N * N, dst, it.ld_recon, it.r, coef, it.vec4 != 0,
-                               dst != nullptr);
-        }
+    const int warp = int(threadIdx.x >> 5);
+    uint8_t *mine = bsm + warp * (BRING * 32 * N * N) + lane * N;
+    float *stage = coef_stage<N>(bsm, warp);
+    walk_units<N>(items, nitems, nunits, warp0, nwarps, lane, mine,
+                  [&](int64_t u, int k, int by, int bx, bool have, const uint8_t *src) {
+                      const BatchItem &it = items[k];
+                      const UnitCoef<N> uc(it, by, bx, lane, stage);
+                      float e = 0.0f;
+                      if (have) {
+                          uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
+                          e = block_any_d<N>(it.slot, it.D, src, dst, it.ld_recon, it.r, uc.mine, uc.vec4,
+                                             dst != nullptr);
+                      }
+                      uc.flush(it, stage, lane);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        unsigned int prev = 0;
-        if (lane == 0) {
-            partials[u] = e;
-            __threadfence();  // the partial is visible before the unit counts as done
-            prev = atomicAdd(done + lo, 1u);
-        }
-        prev = __shfl_sync(0xffffffffu, prev, 0);
-        if (prev + 1 == unsigned(it.nunits)) {  // this warp finished the item's last unit
-            __threadfence();
-            finalize_item(it, partials, sse, psnr, lane);
-            if (lane == 0) done[lo] = 0u;   // ready for the next run of the same batch
-        }
-        slot ^= 1;
-        have = haven;
-        by = byn;
-        bx = bxn;
-        lo = lon;
-        it = itn;
-    }
-    cp_async_wait<0>();
+                      for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                      unsigned int prev = 0;
+                      if (lane == 0) {
+                          partials[u] = e;
+                          __threadfence();  // the partial is visible before the unit counts as done
+                          prev = atomicAdd(done + k, 1u);
+                      }
+                      prev = __shfl_sync(0xffffffffu, prev, 0);
+                      if (prev + 1 == unsigned(it.nunits)) {  // this warp finished the item's last unit
+                          __threadfence();
+                          finalize_item(it, partials, sse, psnr, lane);
+                          if (lane == 0) done[k] = 0u;   // ready for the next run of the same batch
+                      }
+                  });
 }
 
 namespace {
@@ -400,8 +453,11 @@ const void *pick_fn(int D, std::integer_sequence<int, Ds...>) {
     return tab[D];
 }
 
-// Dynamic shared memory of a batch launch: two staging slots per warp.
-size_t batch_smem(int N, int threads) { return size_t(threads / 32) * 2 * 32 * N * N; }
+// Dynamic shared memory of a batch launch: BRING staging slots per warp, and the
+// per-warp coefficient stage for N = 8.
+size_t batch_smem(int N, int threads) {
+    return size_t(threads / 32) * (BRING * 32 * N * N + (N == 8 ? 32 * STG8_LD * 4 : 0));
+}
 
 const void *batch_kernel_for(int N, int D) {
     return N == 4 ? pick_fn<4>(D, std::make_integer_sequence<int, 8>{})
@@ -423,10 +479,27 @@ cudaError_t launch_group(int N, const Group &g, const BatchItem *d_items, float 
     return cudaGetLastError();
 }
 
+const void *queue_kernel_for(int N);
+
+// The staging ring needs more than the default 48 KB of dynamic shared memory: opt
+// every batch kernel of N in, once per device (before its first launch or occupancy
+// query, and so before any graph capture of the launches).
+void batch_smem_attrs(int N, int dev) {
+    static std::mutex mu;
+    static bool done[2][64] = {};
+    const int n = N == 4 ? 0 : 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[n][dev]) return;
+    for (int D = 0; D < 2 * N; D++) ensure_smem_attr(batch_kernel_for(N, D));
+    ensure_smem_attr(queue_kernel_for(N));
+    done[n][dev] = true;
+}
+
 // Largest useful persistent grid for `threads` per CTA and `per_sm` CTAs per SM.
 int grid_for(int N, int threads, int per_sm, int64_t nunits) {
     int dev = 0;
     cudaGetDevice(&dev);
+    batch_smem_attrs(N, dev);
     int occ = 0;
     occ = occupancy(batch_kernel_for(N, N == 4 ? 7 : 15), threads, batch_smem(N, threads));
     const int use = std::max(1, std::min(per_sm, occ));
@@ -471,6 +544,7 @@ const void *queue_kernel_for(int N) {
 int queue_grid(int N, int threads, int per_sm, int64_t nunits) {
     int dev = 0;
     cudaGetDevice(&dev);
+    batch_smem_attrs(N, dev);
     const int occ = occupancy(queue_kernel_for(N), threads, batch_smem(N, threads));
     const int use = std::max(1, std::min(per_sm, occ));
     const int64_t ctas_needed = (nunits * 32 + threads - 1) / threads;
@@ -733,6 +807,11 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
     }
     b->sse = d_sse;
     b->psnr = d_psnr;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        batch_smem_attrs(b->N, dev);   // before any capture of the launches
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int k = 0; k < kBatchSideStreams && e == cudaSuccess; k++) {

@@ -349,11 +349,43 @@ struct TileWalker {
     }
 };
 
+// Per-warp coefficient staging for N = 8: lane l's block writes its r coefficients at
+// stage + l * STG8_LD (16-byte aligned, and lanes 272 bytes apart hit distinct
+// banks); then the warp copies the first nb blocks' runs to dst as one contiguous
+// run of nb * r floats (float4 when vec4).  Called by all 32 lanes.
+constexpr int STG8_LD = 68;
+__device__ __forceinline__ void warp_coef_copy8(float *dst, const float *src, int nb, int r, bool vec4, int lane) {
+    // element c = b n + k of the run (n per block), advanced by 32 without a division
+    if (vec4) {
+        const int n = r >> 2, sb = 32 / n, sk = 32 - sb * n;
+        int b = lane / n, k = lane - b * n;
+        for (int c = lane; c < nb * n; c += 32) {
+            reinterpret_cast<float4 *>(dst)[c] = *reinterpret_cast<const float4 *>(src + b * STG8_LD + 4 * k);
+            b += sb;
+            k += sk;
+            if (k >= n) {
+                k -= n;
+                ++b;
+            }
+        }
+    } else {
+        const int sb = 32 / r, sk = 32 - sb * r;
+        int b = lane / r, k = lane - b * r;
+        for (int c = lane; c < nb * r; c += 32) {
+            dst[c] = src[b * STG8_LD + k];
+            b += sb;
+            k += sk;
+            if (k >= r) {
+                k -= r;
+                ++b;
+            }
+        }
+    }
+}
+
 // N = 8 with any D (one CTA per SM): one block per consumer thread, warp w owning
 // block-row w of the tile (32 blocks, one per lane).  Coefficients are staged per
-// warp in shared memory (block stride STG8_LD floats: 16-byte aligned, and lanes 272
-// bytes apart hit distinct banks) and leave as one contiguous run per block-row.
-constexpr int STG8_LD = 68;
+// warp in shared memory and leave as one contiguous run per block-row.
 template <bool Q>
 __device__ __forceinline__ float tile_reg8_full(const PlanK<8> &P, const FusedGeom &g, uint8_t *tile,
                                                 const TileCoord &tc, int ct, float *Zs) {
@@ -372,33 +404,7 @@ __device__ __forceinline__ float tile_reg8_full(const PlanK<8> &P, const FusedGe
         __syncwarp();
         const int nb = min(BPR, bw - tc.tx * BPR);  // blocks of this block-row inside the image
         float *dst = g.zcoef + (int64_t(tc.img) * g.blocks_per_img + int64_t(gy) * bw + tc.tx * BPR) * r;
-        const float *src = Zs + w * 32 * STG8_LD;
-        // element c = b n + k of the run (n per block), advanced by 32 without a division
-        if (g.coef_vec4) {
-            const int n = r >> 2, sb = 32 / n, sk = 32 - sb * n;
-            int b = lane / n, k = lane - b * n;
-            for (int c = lane; c < nb * n; c += 32) {
-                reinterpret_cast<float4 *>(dst)[c] = *reinterpret_cast<const float4 *>(src + b * STG8_LD + 4 * k);
-                b += sb;
-                k += sk;
-                if (k >= n) {
-                    k -= n;
-                    ++b;
-                }
-            }
-        } else {
-            const int sb = 32 / r, sk = 32 - sb * r;
-            int b = lane / r, k = lane - b * r;
-            for (int c = lane; c < nb * r; c += 32) {
-                dst[c] = src[b * STG8_LD + k];
-                b += sb;
-                k += sk;
-                if (k >= r) {
-                    k -= r;
-                    ++b;
-                }
-            }
-        }
+        warp_coef_copy8(dst, Zs + w * 32 * STG8_LD, nb, r, g.coef_vec4 != 0, lane);
         __syncwarp();  // the staging area is rewritten by the next tile
     }
     return sse;
