@@ -3,12 +3,14 @@
 // Work is a flattened queue of "units": 32 horizontally adjacent N x N blocks of
 // one block-row of one image.  Each warp takes units round-robin; lane l owns
 // block 32u + l and runs the same per-block computation as the fused kernel
-// (block_core: exact column/row pass, zonal mask, inverse, error, 8-bit output)
-// straight from and to global memory with coalesced 8-byte row accesses (a
-// warp's 32 blocks are 256 contiguous bytes per row).  D = diag_bound(N, r) is
-// per image and selects a register-resident variant of block_core.  The SSE of
-// a unit goes to a fixed slot, and a per-image kernel sums an image's slots in
-// order, so results do not depend on the rest of the batch.
+// (block_core: exact column/row pass, zonal mask, inverse, error, 8-bit output).
+// A unit's pixels arrive by cp.async in a per-warp staging ring one unit ahead;
+// the 8-bit output goes straight to global memory (a warp's 32 blocks are 256
+// contiguous bytes per row); for N = 8 the coefficients go through a per-warp
+// shared-memory stage and leave as one contiguous run per unit.  D =
+// diag_bound(N, r) is per image and selects a register-resident variant of
+// block_core.  The SSE of a unit goes to a fixed slot, and a per-image kernel sums
+// an image's slots in order, so results do not depend on the rest of the batch.
 //
 // rklt_fused_items launches immediately (continuous batching of requests);
 // rklt_batch_* builds the queue once, captures the launches in a CUDA graph
