@@ -301,7 +301,9 @@ void rklt_batch_destroy(rklt_batch *b);
 /* Request loop (serving).  A server owns one device buffer of budget_bytes (the
  * device-memory budget requests are admitted against), a pinned host mirror of
  * it, nstreams CUDA streams and result slots for batches of up to max_batch
- * requests; plans (rounded plans, all of one N: 4 or 8) stay host-side and travel
+ * requests, at most two batches in flight per stream (a batch waits for a slot, so
+ * under load later arrivals join the next batch); plans (rounded plans, all of one
+ * N: 4 or 8) stay host-side and travel
  * with each launch.  Creation allocates all of that and runs every kernel both
  * loops can reach once on a small image (so no request pays for module loading);
  * it synchronises the device.  Release with rklt_server_destroy.

@@ -92,7 +92,7 @@ struct rklt_server {
     uint8_t *d_arena = nullptr;
     uint8_t *h_arena = nullptr;         // pinned mirror of the device arena
     std::vector<cudaStream_t> streams;
-    int slots = 0;                      // batches in flight at most
+    int slots = 0;                      // batches in flight at most (two per stream)
     double *d_sse = nullptr;            // [slots][max_batch]
     float *d_psnr = nullptr;
     double *h_sse = nullptr;            // pinned
@@ -380,7 +380,11 @@ rklt_status rklt_server_create(const rklt_plan *const *plans, int nplans, size_t
     }
     s->budget = budget_bytes / 256 * 256;
     s->max_batch = max_batch;
-    s->slots = 64;
+    // two batches in flight per stream: a batch waits for a slot rather than piling
+    // launches onto the streams, so under load the requests that arrive meanwhile
+    // join the next batch (at a 4x stress rate the p99 dropped from hundreds of ms to
+    // a few ms against 64 slots)
+    s->slots = std::min(64, 2 * nstreams);
     cudaError_t e = cudaMalloc(&s->d_arena, s->budget);
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->h_arena), s->budget, cudaHostAllocDefault);
     const size_t nres = size_t(s->slots) * size_t(max_batch);
