@@ -55,7 +55,7 @@ typedef int rklt_status;
 #define RKLT_ERR_OOM 5         /* a library-owned device or host allocation failed    */
 #define RKLT_ERR_BUDGET 6      /* serving: request exceeds the device-memory budget   */
 #define RKLT_ERR_TIMEOUT 7     /* a bounded device-side wait gave up                  */
-#define RKLT_ERR_UNSUPPORTED 8 /* valid request this build does not handle            */
+#define RKLT_ERR_UNSUPPORTED 8 /* valid request the library does not handle          */
 
 /* Thread-local description of the last failure on this host thread. */
 const char *rklt_last_error(void);

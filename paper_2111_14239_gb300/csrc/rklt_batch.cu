@@ -71,10 +71,13 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Position of lane's block in unit u of item it; false past the image's right edge.
+// An item has fewer than 2^31 units (checked when the queue is built), so the
+// division runs in 32 bits.
 __device__ __forceinline__ bool unit_block(const BatchItem &it, int64_t u, int lane, int &by, int &bx) {
-    const int64_t local = u - it.unit_base;
-    by = int(local / it.units_x);
-    bx = int(local - int64_t(by) * it.units_x) * 32 + lane;
+    const uint32_t local = uint32_t(u - it.unit_base);
+    const uint32_t q = local / uint32_t(it.units_x);
+    by = int(q);
+    bx = int(local - q * uint32_t(it.units_x)) * 32 + lane;
     return bx < it.bw;
 }
 
@@ -439,6 +442,7 @@ rklt_status build_groups(const rklt_item *h, int n, const rklt_plan *const *plan
         b.out_index = i;
         b.unit_base = g.nunits;
         b.nunits = int64_t(x.H / N) * b.units_x;
+        if (b.nunits >= (int64_t(1) << 31)) return fail(RKLT_ERR_SHAPE, "image too large for a batch item");
         g.nunits += b.nunits;
         g.items.push_back(b);
     }
