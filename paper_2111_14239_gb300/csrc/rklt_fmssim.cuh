@@ -53,9 +53,7 @@ constexpr int FM_R = 5;           // window radius
 constexpr int FM_WS = 256;        // output columns of a strip (one per thread)
 constexpr int FM_HW = 16;         // halo columns
 constexpr int FM_G = 8;           // horizontal outputs per task
-#ifndef FM_B
-#define FM_B 2
-#endif
+constexpr int FM_B = 2;           // blocks per thread per transform step
 constexpr int FM_HS_BYTES = FM_S * FM_WS * 16;
 constexpr int FM_MAIN_BYTES = FM_SC * FM_WS, FM_HALO_BYTES = FM_SC * FM_HW;
 // shared memory: original (main, halo), reconstruction (main, halo), horizontal
