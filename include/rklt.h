@@ -261,15 +261,15 @@ typedef struct rklt_batch rklt_batch;
  * launch sequence is captured into a CUDA graph and every rklt_batch_run replays it.
  * Two forms of the work exist: one persistent kernel over the whole flattened
  * queue (every plan and r in one launch: units ordered heaviest first, dealt
- * round-robin to the warps, each dispatching on its image's retained support, the
- * per-image SSE / PSNR written by the warp that completes the image's last unit --
- * the graph is then one kernel node), and one launch per (plan, support) group
- * fanned over side streams.  flags bit 0 = autotune: time both forms in several
- * launch shapes (threads per CTA, CTAs per SM) on the batch itself and keep the
- * fastest (rklt_batch_candidates lists what was timed); without it the grouped form
- * runs with 256 threads and one CTA per SM.  (On GB300 the grouped form measured
- * about 2.4x faster for 2000 uneven crops: there each plan's tables are constant-bank
- * operands of the arithmetic, while the queue form must load them by slot index.)  Creation then has run the batch
+ * round-robin to the warps, each dispatching on its image's retained support; then
+ * one finalize kernel writes every image's SSE / PSNR -- two kernel nodes), and one
+ * launch per (plan, support) group fanned over side streams.  flags bit 0 =
+ * autotune: time both forms in several launch shapes (threads per CTA, CTAs per SM)
+ * on the batch itself and keep the fastest (rklt_batch_candidates lists what was
+ * timed); without it the grouped form runs with 256 threads and one CTA per SM.  (On
+ * GB300 the grouped form measured about 1.3x faster for 2000 uneven crops: there
+ * each plan's tables are constant-bank operands of the arithmetic, while the queue
+ * form must load them by slot index.)  Creation then has run the batch
  * several times, overwriting its outputs, and synchronises the device.  The queue
  * form keeps each plan in a constant-memory slot of the device (16 per block size,
  * written on first use, released by rklt_destroy; destroy a plan only after the

@@ -250,12 +250,13 @@ __global__ void batch_finalize(const BatchItem *__restrict__ items, int nitems, 
 }
 
 // ---------------------------------------------------------------------------
-// One persistent launch for a whole batch (all plans, all diagonal bounds).
-// Plans live in a constant-memory table (one slot per plan and device, written once
-// before first use); each unit dispatches on its item's D; the warp that completes
-// an item's last unit sums the item's unit partials in order and writes its SSE and
-// PSNR, then clears the item's counter for the next run.  Units are queued heaviest
-// first (larger D) and dealt round-robin to the warps.
+// One persistent launch for a whole batch (all plans, all diagonal bounds), then one
+// finalize warp per item.  Plans live in a constant-memory table (one slot per plan
+// and device, written once before first use); each unit dispatches on its item's D.
+// Units are queued heaviest first (larger D) and dealt round-robin to the warps.
+// (Finishing an item inside the kernel, by the warp whose unit completes it, needs a
+// fence and an atomic per unit; that made the launch 3x slower than the separate
+// finalize.)
 // ---------------------------------------------------------------------------
 constexpr int kPlanSlots = 16;
 __constant__ PlanK<8> c_plans8[kPlanSlots];
@@ -269,30 +270,30 @@ __device__ __forceinline__ const PlanK<N> &plan_slot(int k) {
 
 // The per-block computation for one diagonal bound, out of line: the queue kernel
 // calls the variant of each unit's D (each variant is compiled once, and the kernel
-// stays a small dispatcher).  src: the staged block, row stride 32 N bytes.
+// stays a small dispatcher).  P: the warp's shared-memory copy of the unit's plan;
+// src: the staged block, row stride 32 N bytes.
 template <int N, int D>
-__device__ __noinline__ float block_d(int slot, const uint8_t *src, uint8_t *dst, int64_t ldd, int r, float *coef,
-                                      bool vec4, bool recon) {
+__device__ __noinline__ float block_d(const PlanK<N> &P, const uint8_t *src, uint8_t *dst, int64_t ldd, int r,
+                                      float *coef, bool vec4, bool recon) {
     uint32_t w[N][N / 4];
     load_block_words<N>(src, 32 * N, w);
-    return block_core<N, D>(plan_slot<N>(slot), w, dst, ldd, r, coef, vec4, recon);
+    return block_core<N, D>(P, w, dst, ldd, r, coef, vec4, recon);
 }
 
 template <int N, int D = 0>
-__device__ __forceinline__ float block_any_d(int slot, int Dr, const uint8_t *src, uint8_t *dst, int64_t ldd, int r,
-                                             float *coef, bool vec4, bool recon) {
+__device__ __forceinline__ float block_any_d(const PlanK<N> &P, int Dr, const uint8_t *src, uint8_t *dst, int64_t ldd,
+                                             int r, float *coef, bool vec4, bool recon) {
     if constexpr (D >= 2 * N - 1) {
-        return block_d<N, 2 * N - 1>(slot, src, dst, ldd, r, coef, vec4, recon);
+        return block_d<N, 2 * N - 1>(P, src, dst, ldd, r, coef, vec4, recon);
     } else {
-        if (Dr == D) return block_d<N, D>(slot, src, dst, ldd, r, coef, vec4, recon);
-        return block_any_d<N, D + 1>(slot, Dr, src, dst, ldd, r, coef, vec4, recon);
+        if (Dr == D) return block_d<N, D>(P, src, dst, ldd, r, coef, vec4, recon);
+        return block_any_d<N, D + 1>(P, Dr, src, dst, ldd, r, coef, vec4, recon);
     }
 }
 
 template <int N>
 __global__ void __launch_bounds__(256, 1)
-    queue_kernel(const BatchItem *__restrict__ items, int nitems, int64_t nunits, float *__restrict__ partials,
-                 unsigned int *__restrict__ done, double *sse, float *psnr) {
+    queue_kernel(const BatchItem *__restrict__ items, int nitems, int64_t nunits, float *__restrict__ partials) {
     extern __shared__ __align__(16) uint8_t bsm[];
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -308,24 +309,13 @@ __global__ void __launch_bounds__(256, 1)
                       float e = 0.0f;
                       if (have) {
                           uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
-                          e = block_any_d<N>(it.slot, it.D, src, dst, it.ld_recon, it.r, uc.mine, uc.vec4,
+                          e = block_any_d<N>(plan_slot<N>(it.slot), it.D, src, dst, it.ld_recon, it.r, uc.mine, uc.vec4,
                                              dst != nullptr);
                       }
                       uc.flush(it, stage, lane);
 #pragma unroll
                       for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-                      unsigned int prev = 0;
-                      if (lane == 0) {
-                          partials[u] = e;
-                          __threadfence();  // the partial is visible before the unit counts as done
-                          prev = atomicAdd(done + k, 1u);
-                      }
-                      prev = __shfl_sync(0xffffffffu, prev, 0);
-                      if (prev + 1 == unsigned(it.nunits)) {  // this warp finished the item's last unit
-                          __threadfence();
-                          finalize_item(it, partials, sse, psnr, lane);
-                          if (lane == 0) done[k] = 0u;   // ready for the next run of the same batch
-                      }
+                      if (lane == 0) partials[u] = e;
                   });
 }
 
@@ -565,15 +555,18 @@ __global__ void empty_items(const BatchItem *__restrict__ items, int n, double *
     psnr[items[i].out_index] = __int_as_float(0x7fc00000);
 }
 
+// The queue kernel over every unit, then one finalize warp per item (the unit
+// partials summed in order, as for the grouped launches).
 cudaError_t launch_queue(int N, const BatchItem *d_items, int nitems, int64_t nunits, const BatchItem *d_empty,
-                         int nempty, float *partials, unsigned int *done, double *sse, float *psnr, int threads,
-                         int per_sm, cudaStream_t st) {
+                         int nempty, float *partials, double *sse, float *psnr, int threads, int per_sm,
+                         cudaStream_t st) {
     if (nunits > 0) {
         const int grid = queue_grid(N, threads, per_sm, nunits);
-        void *args[] = {&d_items, &nitems, &nunits, &partials, &done, &sse, &psnr};
+        void *args[] = {&d_items, &nitems, &nunits, &partials};
         const cudaError_t e =
             cudaLaunchKernel(queue_kernel_for(N), dim3(grid), dim3(threads), args, batch_smem(N, threads), st);
         if (e != cudaSuccess) return e;
+        batch_finalize<<<nitems, 32, 0, st>>>(d_items, nitems, nunits, partials, sse, psnr);
     }
     if (nempty > 0) empty_items<<<(nempty + 127) / 128, 128, 0, st>>>(d_empty, nempty, sse, psnr);
     return cudaGetLastError();
@@ -610,7 +603,6 @@ struct rklt_batch {
     int q_items = 0, q_empty = 0;
     rklt::BatchItem *dq_items = nullptr, *dq_empty = nullptr;
     float *dq_partials = nullptr;
-    unsigned int *dq_done = nullptr;
 };
 
 using namespace rklt;
@@ -626,7 +618,6 @@ void batch_free(rklt_batch *b) {
     cudaFree(b->dq_items);
     cudaFree(b->dq_empty);
     cudaFree(b->dq_partials);
-    cudaFree(b->dq_done);
     if (b->stream) cudaStreamDestroy(b->stream);
     for (auto s : b->side) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
@@ -642,7 +633,7 @@ cudaError_t batch_enqueue_groups(rklt_batch *b, int threads, int per_sm, cudaStr
 cudaError_t batch_enqueue(rklt_batch *b, int mode, int threads, int per_sm, cudaStream_t st) {
     if (mode == 1)
         return launch_queue(b->N, b->dq_items, b->q_items, b->q_units, b->dq_empty, b->q_empty, b->dq_partials,
-                            b->dq_done, b->sse, b->psnr, threads, per_sm, st);
+                            b->sse, b->psnr, threads, per_sm, st);
     return batch_enqueue_groups(b, threads, per_sm, st);
 }
 
@@ -845,7 +836,7 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
                                               : cuda_fail(e, "batch set-up");
     }
     // the whole batch as one queue for the persistent kernel (when every plan gets a
-    // constant-memory slot); its item counters start at zero and each run leaves them so
+    // constant-memory slot)
     bool queue_ok = false;
     if (e == cudaSuccess) {
         std::vector<BatchItem> q, em;
@@ -856,12 +847,10 @@ rklt_status rklt_batch_create(const rklt_item *h_items, int n, const rklt_plan *
             e = cudaMalloc(&b->dq_items, std::max<size_t>(q.size(), 1) * sizeof(BatchItem));
             if (e == cudaSuccess) e = cudaMalloc(&b->dq_empty, std::max<size_t>(em.size(), 1) * sizeof(BatchItem));
             if (e == cudaSuccess) e = cudaMalloc(&b->dq_partials, size_t(std::max<int64_t>(b->q_units, 1)) * 4);
-            if (e == cudaSuccess) e = cudaMalloc(&b->dq_done, std::max<size_t>(q.size(), 1) * sizeof(unsigned int));
             if (e == cudaSuccess && !q.empty())
                 e = cudaMemcpy(b->dq_items, q.data(), q.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
             if (e == cudaSuccess && !em.empty())
                 e = cudaMemcpy(b->dq_empty, em.data(), em.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemset(b->dq_done, 0, std::max<size_t>(q.size(), 1) * sizeof(unsigned int));
         }
     }
     if (e != cudaSuccess) {
