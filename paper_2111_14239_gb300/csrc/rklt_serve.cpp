@@ -17,9 +17,13 @@
 //
 // Both record, per request, the completion time on the same clock as the arrivals.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -81,6 +85,92 @@ Layout layout_of(const rklt_request &q, int N) {
     return L;
 }
 
+// Host staging copies of one admitted batch, spread over worker threads: the loop
+// thread publishes the batch's row chunks and copies alongside the workers, then
+// waits until every worker has finished with them.  Under load one core's memcpy
+// bandwidth would otherwise bound how fast admitted images reach pinned memory.
+class CopyPool {
+  public:
+    struct Chunk {
+        uint8_t *dst;          // pinned, pitch ld
+        const uint8_t *src;    // caller's image rows, pitch W
+        int64_t ld;
+        int W, rows;
+    };
+    explicit CopyPool(int workers) : n_(workers) {
+        for (int k = 0; k < workers; k++) th_.emplace_back([this] { loop(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    void run(const Chunk *c, size_t n) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            jobs_ = c;
+            njobs_ = n;
+            next_.store(0, std::memory_order_relaxed);
+            acked_ = 0;
+            ++gen_;
+        }
+        cv_.notify_all();
+        drain(c, n);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return acked_ == n_; });
+    }
+
+  private:
+    static void copy(const Chunk &k) {
+        if (k.ld == k.W) {
+            std::memcpy(k.dst, k.src, size_t(k.rows) * size_t(k.W));
+            return;
+        }
+        for (int y = 0; y < k.rows; y++)
+            std::memcpy(k.dst + size_t(y) * size_t(k.ld), k.src + size_t(y) * size_t(k.W), size_t(k.W));
+    }
+    void drain(const Chunk *c, size_t n) {
+        for (size_t i = next_.fetch_add(1, std::memory_order_relaxed); i < n;
+             i = next_.fetch_add(1, std::memory_order_relaxed))
+            copy(c[i]);
+    }
+    void loop() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            if (stop_) return;
+            const Chunk *c = jobs_;
+            const size_t n = njobs_;
+            lk.unlock();
+            drain(c, n);
+            lk.lock();
+            if (++acked_ == n_) done_cv_.notify_all();
+        }
+    }
+    const int n_;
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    const Chunk *jobs_ = nullptr;
+    size_t njobs_ = 0;
+    std::atomic<size_t> next_{0};
+    int acked_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+// Batches whose images total at least this many bytes are staged by the pool; smaller
+// ones by the loop thread alone (waking the workers costs more than it saves there).
+constexpr size_t kPoolBytes = size_t(2) << 20;
+constexpr int kChunkBytes = 1 << 20;   // rows per chunk: about 1 MB of pixels
+constexpr int kCopyWorkers = 3;
+
 }  // namespace
 }  // namespace rklt
 
@@ -98,6 +188,7 @@ struct rklt_server {
     double *h_sse = nullptr;            // pinned
     float *h_psnr = nullptr;
     std::vector<cudaEvent_t> events;    // one per slot
+    std::unique_ptr<rklt::CopyPool> pool;   // staging copies of large batches
 };
 
 using namespace rklt;
@@ -170,6 +261,7 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
     std::deque<int> waiting;
     std::vector<Inflight> inflight;
     std::vector<rklt_item> items;
+    std::vector<CopyPool::Chunk> chunks;
     std::vector<Layout> lay(static_cast<size_t>(n));
     for (int i = 0; i < n; i++) lay[size_t(i)] = layout_of(q[i], s->N);
     int next_stream = 0, k = 0, completed = 0;
@@ -204,12 +296,32 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
             free_slots.pop_back();
             items.clear();
             cudaError_t e = cudaSuccess;
+            // the admitted images into their pinned slots (by the pool when large)
+            size_t bytes = 0;
+            for (size_t b = 0; b < batch.size(); b++) bytes += size_t(q[batch[b]].H) * size_t(q[batch[b]].W);
+            if (s->pool && bytes >= kPoolBytes) {
+                chunks.clear();
+                for (size_t b = 0; b < batch.size(); b++) {
+                    const rklt_request &r = q[batch[b]];
+                    const Layout &L = lay[size_t(batch[b])];
+                    const int step = std::max(1, kChunkBytes / r.W);
+                    for (int y = 0; y < r.H; y += step)
+                        chunks.push_back({s->h_arena + offs[b] + L.in + size_t(y) * size_t(L.ld),
+                                          r.h_img + size_t(y) * size_t(r.W), L.ld, r.W, std::min(step, r.H - y)});
+                }
+                s->pool->run(chunks.data(), chunks.size());
+            } else {
+                for (size_t b = 0; b < batch.size(); b++) {
+                    const rklt_request &r = q[batch[b]];
+                    copy_rows(s->h_arena + offs[b] + lay[size_t(batch[b])].in, lay[size_t(batch[b])].ld, r.h_img, r.H,
+                              r.W);
+                }
+            }
             for (size_t b = 0; b < batch.size(); b++) {
                 const rklt_request &r = q[batch[b]];
                 const Layout &L = lay[size_t(batch[b])];
                 uint8_t *h = s->h_arena + offs[b];
                 uint8_t *d = s->d_arena + offs[b];
-                copy_rows(h + L.in, L.ld, r.h_img, r.H, r.W);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(d + L.in, h + L.in, size_t(r.H) * size_t(L.ld), cudaMemcpyHostToDevice, st);
                 rklt_item it{};
@@ -385,6 +497,11 @@ rklt_status rklt_server_create(const rklt_plan *const *plans, int nplans, size_t
     // join the next batch (at a 4x stress rate the p99 dropped from hundreds of ms to
     // a few ms against 64 slots)
     s->slots = std::min(64, 2 * nstreams);
+    try {
+        s->pool.reset(new CopyPool(kCopyWorkers));
+    } catch (...) {
+        s->pool.reset();   // no worker threads: the loop stages every batch itself
+    }
     cudaError_t e = cudaMalloc(&s->d_arena, s->budget);
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->h_arena), s->budget, cudaHostAllocDefault);
     const size_t nres = size_t(s->slots) * size_t(max_batch);
