@@ -741,6 +741,27 @@ class ItemRing {
 std::mutex g_ring_mu;
 ItemRing g_ring[64];  // per device
 
+// Item descriptors to the device through the pinned ring (pageable when the ring is
+// full, or under stream capture, where the copy would run at replay after the region
+// is reused).
+cudaError_t copy_items(BatchItem *d_items, const BatchItem *h_items, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_ring_mu);
+    ItemRing &ring = g_ring[dev >= 0 && dev < 64 ? dev : 0];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    void *pinned = cs == cudaStreamCaptureStatusNone ? ring.get(bytes) : nullptr;
+    if (!pinned) return cudaMemcpyAsync(d_items, h_items, bytes, cudaMemcpyHostToDevice, st);
+    std::memcpy(pinned, h_items, bytes);
+    const cudaError_t e = cudaMemcpyAsync(d_items, pinned, bytes, cudaMemcpyHostToDevice, st);
+    ring.done(st);
+    return e;
+}
+
+// Immediate batches with at least this many groups take the one-launch queue form.
+constexpr size_t kQueueGroups = 3;
+
 }  // namespace
 
 extern "C" {
@@ -755,6 +776,32 @@ rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *c
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaMemPool_t pool = scratch_pool();
     if (!pool) return fail(RKLT_ERR_CUDA, "could not create the scratch memory pool");
+    // Several (plan, support) groups: one queue launch and one finalize for all of them
+    // instead of a launch pair per group (fewer commands on the stream; a request loop
+    // issuing a batch per pass otherwise fills the stream's command queue and blocks).
+    if (groups.size() >= kQueueGroups) {
+        std::vector<BatchItem> q, em;
+        int64_t nunits = 0;
+        if (build_queue(groups, q, em, nunits)) {
+            std::vector<BatchItem> all(q);
+            all.insert(all.end(), em.begin(), em.end());
+            const size_t ab = all.size() * sizeof(BatchItem);
+            const size_t off_p = (ab + 255) & ~size_t(255);
+            const size_t pb = size_t(std::max<int64_t>(nunits, 1)) * sizeof(float);
+            void *scratch = nullptr;
+            if (cudaMallocFromPoolAsync(&scratch, off_p + pb, pool, st) != cudaSuccess)
+                return fail(RKLT_ERR_OOM, "scratch allocation failed");
+            BatchItem *d_all = static_cast<BatchItem *>(scratch);
+            float *partials = reinterpret_cast<float *>(static_cast<char *>(scratch) + off_p);
+            cudaError_t e = copy_items(d_all, all.data(), ab, st);
+            if (e == cudaSuccess)
+                e = launch_queue(N, d_all, int(q.size()), nunits, d_all + q.size(), int(em.size()), partials, d_sse,
+                                 d_psnr, 256, 1, st);
+            cudaFreeAsync(scratch, st);
+            if (e != cudaSuccess) return cuda_fail(e, "queued launch");
+            return RKLT_OK;
+        }
+    }
     for (const Group &g : groups) {
         const size_t ib = g.items.size() * sizeof(BatchItem);
         const size_t pb = size_t(std::max<int64_t>(g.nunits, 1)) * sizeof(float);
@@ -764,24 +811,7 @@ rklt_status rklt_fused_items(const rklt_item *h_items, int n, const rklt_plan *c
         BatchItem *d_items = static_cast<BatchItem *>(scratch);
         float *partials = reinterpret_cast<float *>(static_cast<char *>(scratch) + ib);
         // descriptors through the pinned ring (an asynchronous copy); pageable if it is full
-        cudaError_t e = cudaSuccess;
-        {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            std::lock_guard<std::mutex> lk(g_ring_mu);
-            ItemRing &ring = g_ring[dev >= 0 && dev < 64 ? dev : 0];
-            // under stream capture the copy would run at replay, after the region is reused
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            cudaStreamIsCapturing(st, &cs);
-            void *pinned = cs == cudaStreamCaptureStatusNone ? ring.get(ib) : nullptr;
-            if (pinned) {
-                std::memcpy(pinned, g.items.data(), ib);
-                e = cudaMemcpyAsync(d_items, pinned, ib, cudaMemcpyHostToDevice, st);
-                ring.done(st);
-            } else {
-                e = cudaMemcpyAsync(d_items, g.items.data(), ib, cudaMemcpyHostToDevice, st);
-            }
-        }
+        cudaError_t e = copy_items(d_items, g.items.data(), ib, st);
         if (e == cudaSuccess)
             e = launch_group(N, g, d_items, partials, d_sse, d_psnr, 256, grid_for(N, 256, 1, g.nunits), st);
         cudaFreeAsync(scratch, st);

@@ -262,6 +262,8 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
     std::vector<Inflight> inflight;
     std::vector<rklt_item> items;
     std::vector<CopyPool::Chunk> chunks;
+    std::vector<std::pair<size_t, size_t>> runs;   // (first, last) batch positions of a contiguous run
+    std::vector<size_t> order;
     std::vector<Layout> lay(static_cast<size_t>(n));
     for (int i = 0; i < n; i++) lay[size_t(i)] = layout_of(q[i], s->N);
     int next_stream = 0, k = 0, completed = 0;
@@ -317,13 +319,36 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
                               r.W);
                 }
             }
+            // copies as few contiguous spans as possible: slots that touch in the arena
+            // form one run, copied in one call per direction (a run holds only this
+            // batch's slots).  One call per request and direction filled the stream's
+            // command queue at high rates, and the host then blocked for hundreds of ms.
+            runs.clear();
+            order.resize(batch.size());
+            for (size_t b = 0; b < batch.size(); b++) order[b] = b;
+            std::sort(order.begin(), order.end(), [&](size_t a, size_t b2) { return offs[a] < offs[b2]; });
+            for (size_t t = 0; t < order.size(); t++) {
+                const size_t b = order[t];
+                if (!runs.empty()) {
+                    const size_t p = runs.back().second;
+                    if (offs[p] + lay[size_t(batch[p])].total == offs[b]) {
+                        runs.back().second = b;
+                        continue;
+                    }
+                }
+                runs.push_back({b, b});
+            }
+            for (const auto &run : runs) {
+                const Layout &Lf = lay[size_t(batch[run.first])], &Ll = lay[size_t(batch[run.second])];
+                const size_t from = offs[run.first] + Lf.in;
+                const size_t to = offs[run.second] + Ll.in + size_t(q[batch[run.second]].H) * size_t(Ll.ld);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(s->d_arena + from, s->h_arena + from, to - from, cudaMemcpyHostToDevice, st);
+            }
             for (size_t b = 0; b < batch.size(); b++) {
                 const rklt_request &r = q[batch[b]];
                 const Layout &L = lay[size_t(batch[b])];
-                uint8_t *h = s->h_arena + offs[b];
                 uint8_t *d = s->d_arena + offs[b];
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(d + L.in, h + L.in, size_t(r.H) * size_t(L.ld), cudaMemcpyHostToDevice, st);
                 rklt_item it{};
                 it.d_img = d + L.in;
                 it.H = r.H;
@@ -342,14 +367,11 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
             const rklt_status ls = rklt_fused_items(items.data(), int(items.size()), s->plans.data(),
                                                     int(s->plans.size()), dsse, dps, st);
             if (ls != RKLT_OK) return ls;
-            for (size_t b = 0; b < batch.size() && e == cudaSuccess; b++) {
-                const rklt_request &r = q[batch[b]];
-                const Layout &L = lay[size_t(batch[b])];
-                e = cudaMemcpyAsync(s->h_arena + offs[b] + L.rec, s->d_arena + offs[b] + L.rec,
-                                    size_t(r.H) * size_t(L.ld), cudaMemcpyDeviceToHost, st);
-                if (e == cudaSuccess && r.r > 0)
-                    e = cudaMemcpyAsync(s->h_arena + offs[b] + L.coef, s->d_arena + offs[b] + L.coef,
-                                        L.total - L.coef, cudaMemcpyDeviceToHost, st);
+            for (const auto &run : runs) {
+                if (e != cudaSuccess) break;
+                const Layout &Lf = lay[size_t(batch[run.first])], &Ll = lay[size_t(batch[run.second])];
+                const size_t from = offs[run.first] + Lf.rec, to = offs[run.second] + Ll.total;
+                e = cudaMemcpyAsync(s->h_arena + from, s->d_arena + from, to - from, cudaMemcpyDeviceToHost, st);
             }
             const size_t nb = batch.size();
             if (e == cudaSuccess)
