@@ -240,10 +240,14 @@ typedef struct rklt_item {
 } rklt_item;
 
 /* Immediate batched pass: rklt_fused (Sec. 4.1, Appendix) for images of uneven
- * sizes, each with its own plan and r.  Items are grouped by plan; per group one
- * launch of a persistent kernel over a flattened queue of 32-block units of all its images
- * (warp per unit, each lane one block, coalesced row accesses), then a per-image
- * SSE / PSNR kernel.  d_sse[i], d_psnr[i] receive item i's results; they are
+ * sizes, each with its own plan and r.  Items are grouped by (plan, retained
+ * support); per group one launch of a persistent kernel over a flattened queue of
+ * 32-block units of all its images (warp per unit, each lane one block, coalesced row
+ * accesses), then a per-image SSE / PSNR kernel; with three or more groups, one launch
+ * of the queue kernel over every group's units (plans from a constant-memory table,
+ * written on first use) and one SSE / PSNR kernel instead, so that a caller issuing
+ * many small batches queues few commands.  d_sse[i], d_psnr[i] receive item i's
+ * results; they are
  * bit-identical to what a batch of item i alone produces.  Scratch (descriptors,
  * per-unit partials) comes from a stream-ordered pool; the descriptors travel
  * through a library-owned pinned ring (4 MB per device, reused once the copy
