@@ -259,13 +259,19 @@ __global__ void batch_finalize(const BatchItem *__restrict__ items, int nitems, 
 // finalize.)
 // ---------------------------------------------------------------------------
 constexpr int kPlanSlots = 16;
-__constant__ PlanK<8> c_plans8[kPlanSlots];
-__constant__ PlanK<4> c_plans4[kPlanSlots];
+// Each slot padded to whole 256-byte lines, so that no cached constant line holds
+// bytes of two plans (a slot is written while kernels reading other slots may run).
+template <int N>
+struct alignas(256) PlanSlot {
+    PlanK<N> k;
+};
+__constant__ PlanSlot<8> c_plans8[kPlanSlots];
+__constant__ PlanSlot<4> c_plans4[kPlanSlots];
 
 template <int N>
 __device__ __forceinline__ const PlanK<N> &plan_slot(int k) {
-    if constexpr (N == 8) return c_plans8[k];
-    else return c_plans4[k];
+    if constexpr (N == 8) return c_plans8[k].k;
+    else return c_plans4[k].k;
 }
 
 // The per-block computation for one diagonal bound, out of line: the queue kernel
@@ -345,7 +351,7 @@ int plan_slot_for(const Plan &p) {
     static cudaStream_t up[64] = {};
     if (!up[dev] && cudaStreamCreateWithFlags(&up[dev], cudaStreamNonBlocking) != cudaSuccess) return -1;
     const size_t bytes = p.N == 8 ? sizeof(PlanK<8>) : sizeof(PlanK<4>);
-    const size_t off = size_t(free_k) * bytes;
+    const size_t off = size_t(free_k) * (p.N == 8 ? sizeof(PlanSlot<8>) : sizeof(PlanSlot<4>));
     const cudaError_t e = p.N == 8 ? cudaMemcpyToSymbolAsync(c_plans8, p.k.data(), bytes, off,
                                                               cudaMemcpyHostToDevice, up[dev])
                                    : cudaMemcpyToSymbolAsync(c_plans4, p.k.data(), bytes, off,

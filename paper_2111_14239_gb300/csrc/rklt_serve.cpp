@@ -251,6 +251,7 @@ struct Inflight {
     int slot;
     std::vector<int> reqs;
     std::vector<size_t> offs;
+    size_t block_off, block_len;   // the batch's arena block
 };
 
 rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t *const *h_recon,
@@ -264,6 +265,7 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
     std::vector<CopyPool::Chunk> chunks;
     std::vector<std::pair<size_t, size_t>> runs;   // (first, last) batch positions of a contiguous run
     std::vector<size_t> order;
+    std::vector<size_t> prefix;
     std::vector<Layout> lay(static_cast<size_t>(n));
     for (int i = 0; i < n; i++) lay[size_t(i)] = layout_of(q[i], s->N);
     int next_stream = 0, k = 0, completed = 0;
@@ -272,24 +274,42 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
         const double now = seconds_since(t0);
         while (k < n && q[k].arrival_s <= now) waiting.push_back(k++);
         // admission by budget, first come first served; a request larger than the
-        // whole budget is rejected
+        // whole budget is rejected.  A batch takes one contiguous arena block (its
+        // requests' slots back to back), the longest prefix of the waiting requests
+        // that fits, so that its copies are one call per direction whatever the
+        // arena's fragmentation.
         std::vector<int> batch;
         std::vector<size_t> offs;
-        while (!waiting.empty() && int(batch.size()) < s->max_batch && !free_slots.empty()) {
+        size_t block_off = 0, block_len = 0;
+        while (!waiting.empty() && lay[size_t(waiting.front())].total > s->budget) {
             const int i = waiting.front();
-            const size_t need = lay[size_t(i)].total;
-            if (need > s->budget) {
-                waiting.pop_front();
-                res[i].status = RKLT_ERR_BUDGET;
-                res[i].done_s = now;
-                completed++;
-                continue;
-            }
-            size_t off = 0;
-            if (!arena.alloc(need, off)) break;
             waiting.pop_front();
-            batch.push_back(i);
-            offs.push_back(off);
+            res[i].status = RKLT_ERR_BUDGET;
+            res[i].done_s = now;
+            completed++;
+        }
+        if (!waiting.empty() && !free_slots.empty()) {
+            size_t cand = 0, total = 0;
+            prefix.clear();
+            while (cand < waiting.size() && int(cand) < s->max_batch) {
+                const size_t t = lay[size_t(waiting[cand])].total;
+                if (t > s->budget) break;   // rejected when it reaches the front
+                total += t;
+                prefix.push_back(total);
+                cand++;
+            }
+            while (cand > 0 && !arena.alloc(prefix[cand - 1], block_off)) cand--;
+            if (cand > 0) {
+                block_len = prefix[cand - 1];
+                size_t off = block_off;
+                for (size_t c = 0; c < cand; c++) {
+                    const int i = waiting.front();
+                    waiting.pop_front();
+                    batch.push_back(i);
+                    offs.push_back(off);
+                    off += lay[size_t(i)].total;
+                }
+            }
         }
         if (!batch.empty()) {
             const cudaStream_t st = s->streams[size_t(next_stream)];
@@ -384,7 +404,7 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
             if (e != cudaSuccess) return cuda_fail(e, "request launch");
             const double tl = seconds_since(t0);
             for (int i : batch) res[i].admit_s = tl;
-            inflight.push_back({slot, std::move(batch), std::move(offs)});
+            inflight.push_back({slot, std::move(batch), std::move(offs), block_off, block_len});
         }
         // completions
         for (size_t f = 0; f < inflight.size();) {
@@ -408,9 +428,9 @@ rklt_status run_continuous(rklt_server *s, const rklt_request *q, int n, uint8_t
                 if (h_coef && h_coef[i] && q[i].r > 0)
                     std::memcpy(h_coef[i], s->h_arena + it.offs[b] + L.coef,
                                 size_t(q[i].H / s->N) * size_t(q[i].W / s->N) * size_t(q[i].r) * sizeof(float));
-                arena.release(it.offs[b], L.total);
                 completed++;
             }
+            arena.release(it.block_off, it.block_len);
             free_slots.push_back(it.slot);
             inflight.erase(inflight.begin() + long(f));
         }
