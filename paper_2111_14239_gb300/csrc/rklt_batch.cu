@@ -276,24 +276,25 @@ __device__ __forceinline__ const PlanK<N> &plan_slot(int k) {
 
 // The per-block computation for one diagonal bound, out of line: the queue kernel
 // calls the variant of each unit's D (each variant is compiled once, and the kernel
-// stays a small dispatcher).  P: the warp's shared-memory copy of the unit's plan;
-// src: the staged block, row stride 32 N bytes.
+// stays a small dispatcher).  slot: the unit's plan in the constant-memory table,
+// read inside so that its operands are constant-bank loads; src: the staged block,
+// row stride 32 N bytes.
 template <int N, int D>
-__device__ __noinline__ float block_d(const PlanK<N> &P, const uint8_t *src, uint8_t *dst, int64_t ldd, int r,
-                                      float *coef, bool vec4, bool recon) {
+__device__ __noinline__ float block_d(int slot, const uint8_t *src, uint8_t *dst, int64_t ldd, int r, float *coef,
+                                      bool vec4, bool recon) {
     uint32_t w[N][N / 4];
     load_block_words<N>(src, 32 * N, w);
-    return block_core<N, D>(P, w, dst, ldd, r, coef, vec4, recon);
+    return block_core<N, D>(plan_slot<N>(slot), w, dst, ldd, r, coef, vec4, recon);
 }
 
 template <int N, int D = 0>
-__device__ __forceinline__ float block_any_d(const PlanK<N> &P, int Dr, const uint8_t *src, uint8_t *dst, int64_t ldd,
-                                             int r, float *coef, bool vec4, bool recon) {
+__device__ __forceinline__ float block_any_d(int slot, int Dr, const uint8_t *src, uint8_t *dst, int64_t ldd, int r,
+                                             float *coef, bool vec4, bool recon) {
     if constexpr (D >= 2 * N - 1) {
-        return block_d<N, 2 * N - 1>(P, src, dst, ldd, r, coef, vec4, recon);
+        return block_d<N, 2 * N - 1>(slot, src, dst, ldd, r, coef, vec4, recon);
     } else {
-        if (Dr == D) return block_d<N, D>(P, src, dst, ldd, r, coef, vec4, recon);
-        return block_any_d<N, D + 1>(P, Dr, src, dst, ldd, r, coef, vec4, recon);
+        if (Dr == D) return block_d<N, D>(slot, src, dst, ldd, r, coef, vec4, recon);
+        return block_any_d<N, D + 1>(slot, Dr, src, dst, ldd, r, coef, vec4, recon);
     }
 }
 
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(256, 1)
                       float e = 0.0f;
                       if (have) {
                           uint8_t *dst = it.recon ? it.recon + int64_t(by) * N * it.ld_recon + bx * N : nullptr;
-                          e = block_any_d<N>(plan_slot<N>(it.slot), it.D, src, dst, it.ld_recon, it.r, uc.mine, uc.vec4,
+                          e = block_any_d<N>(it.slot, it.D, src, dst, it.ld_recon, it.r, uc.mine, uc.vec4,
                                              dst != nullptr);
                       }
                       uc.flush(it, stage, lane);
