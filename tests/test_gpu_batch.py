@@ -83,7 +83,8 @@ def test_items_against_oracle_and_alone(rk, orc, N):
         check_recon_u8(mix[i][1], rref, N)
         if sref > 0 and sse_h[i] > 0:
             assert ps_h[i] == pytest.approx(10 * math.log10(255 ** 2 * H * W / sse_h[i]), abs=1e-4)
-    # alone: a batch of one item gives bit-identical outputs
+    # alone: a batch of one item gives bit-identical outputs (the mix, with more than
+    # three (plan, support) groups, ran as one queue launch; one item runs as one group)
     for i in (0, 3, 17, 29):
         one = rk.make_items([entries[i]])
         s1 = torch.zeros(1, dtype=torch.float64, device="cuda")
