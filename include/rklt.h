@@ -365,6 +365,13 @@ void rklt_server_destroy(rklt_server *s);
  * everything does not coalesce the free list back into one range. */
 rklt_status rklt_arena_selftest(unsigned seed, int steps);
 
+/* Host-only check of the worker pool that stages large batches' images into pinned
+ * memory (no GPU needed): `rounds` batches of random images with random pitches, cut
+ * into row chunks, copied by the pool; fails (RKLT_ERR_ARG, message in
+ * rklt_last_error) if a destination row differs from its source or a copy touches
+ * the pitch padding.  Starts and joins three worker threads. */
+rklt_status rklt_copypool_selftest(unsigned seed, int rounds);
+
 /* r-sweep: for nimg same-shape images and nplans plans (all with the same N, 4 or
  * 8), the SSE and PSNR of the reconstruction that keeps the first r zig-zag
  * coefficients, for every r = 1..N*N (Sec. 4.1 zonal retention swept over r, as

@@ -104,6 +104,7 @@ _SIGS = {
     "rklt_server_run": (_I, [_P, _P, _I, _I, _P, _P, _P, ctypes.POINTER(_D)]),
     "rklt_server_destroy": (None, [_P]),
     "rklt_arena_selftest": (_I, [ctypes.c_uint, _I]),
+    "rklt_copypool_selftest": (_I, [ctypes.c_uint, _I]),
     "rklt_set_wait_timeout_us": (None, [_U32]),
     "rklt_set_transport": (None, [_I]),
     "rklt_set_tensor_engine": (None, [_I]),

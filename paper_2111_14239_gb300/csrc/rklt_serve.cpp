@@ -592,6 +592,70 @@ rklt_status rklt_server_run(rklt_server *s, const rklt_request *reqs, int n, int
 
 void rklt_server_destroy(rklt_server *s) { server_free(s); }
 
+rklt_status rklt_copypool_selftest(unsigned seed, int rounds) {
+    // rounds of staging copies through a pool of worker threads: random images with
+    // random pitches cut into row chunks of random height; every destination row must
+    // hold its source row and the pitch padding must keep its sentinel byte
+    unsigned x = seed ? seed : 1u;
+    auto rnd = [&x]() {
+        x ^= x << 13;
+        x ^= x >> 17;
+        x ^= x << 5;
+        return x;
+    };
+    std::unique_ptr<rklt::CopyPool> pool;
+    try {
+        pool.reset(new rklt::CopyPool(3));
+    } catch (...) {
+        return fail(RKLT_ERR_ARG, "could not start the copy workers");
+    }
+    std::vector<uint8_t> src, dst;
+    std::vector<rklt::CopyPool::Chunk> chunks;
+    struct Img {
+        size_t s_off, d_off;
+        int H, W;
+        int64_t ld;
+    };
+    std::vector<Img> imgs;
+    for (int t = 0; t < rounds; t++) {
+        imgs.clear();
+        chunks.clear();
+        size_t s_len = 0, d_len = 0;
+        const int nimg = 1 + int(rnd() % 6);
+        for (int i = 0; i < nimg; i++) {
+            Img m{};
+            m.H = 1 + int(rnd() % 97);
+            m.W = 1 + int(rnd() % 301);
+            m.ld = m.W + int64_t(rnd() % 17);
+            m.s_off = s_len;
+            m.d_off = d_len;
+            s_len += size_t(m.H) * size_t(m.W);
+            d_len += size_t(m.H) * size_t(m.ld);
+            imgs.push_back(m);
+        }
+        src.resize(s_len);
+        for (auto &b : src) b = uint8_t(rnd());
+        dst.assign(d_len, 0xA5);
+        for (const Img &m : imgs) {
+            const int step = 1 + int(rnd() % 13);
+            for (int y = 0; y < m.H; y += step)
+                chunks.push_back({dst.data() + m.d_off + size_t(y) * size_t(m.ld), src.data() + m.s_off + size_t(y) * m.W,
+                                  m.ld, m.W, std::min(step, m.H - y)});
+        }
+        pool->run(chunks.data(), chunks.size());
+        for (const Img &m : imgs)
+            for (int y = 0; y < m.H; y++) {
+                const uint8_t *d = dst.data() + m.d_off + size_t(y) * size_t(m.ld);
+                if (std::memcmp(d, src.data() + m.s_off + size_t(y) * m.W, size_t(m.W)) != 0)
+                    return fail(RKLT_ERR_ARG, "a staged row differs from its source");
+                for (int64_t c = m.W; c < m.ld; c++)
+                    if (d[c] != 0xA5) return fail(RKLT_ERR_ARG, "a copy wrote into the pitch padding");
+            }
+    }
+    pool.reset();   // joins the workers
+    return RKLT_OK;
+}
+
 rklt_status rklt_arena_selftest(unsigned seed, int steps) {
     // random allocations and releases against a byte map of the arena: no two live
     // ranges overlap, offsets are 256-byte aligned, and releasing everything

@@ -7,6 +7,14 @@ serve = pytest.importorskip("paper_2111_14239_gb300.serve")
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
+def test_native_copy_pool_stages_every_row(seed):
+    """The request loop's staging workers: many rounds in a row (each round hands the
+    workers a new set of chunks), every row copied exactly, padding untouched."""
+    st = rk.lib.rklt_copypool_selftest(seed, 300)
+    assert st == 0, rk.lib.rklt_last_error()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
 def test_native_arena_never_overlaps_and_coalesces(seed):
     st = rk.lib.rklt_arena_selftest(seed, 5000)
     assert st == 0, rk.lib.rklt_last_error()
