@@ -74,3 +74,32 @@ def test_argument_checks_without_gpu():
     assert rk.lib.rklt_fused(plan.handle, d, 16, 16, 16, 10, None, None, 0, None, d, None) == 1
     assert rk.lib.rklt_zonal(plan.handle, d, 4, 10, d, None) == 1                           # aliasing, r < 64
     assert rk.lib.rklt_fused_batched(plan.handle, d, 2, 16, 16, 16, 100, 10, None, None, 0, 0, d, d, None) == 2
+
+
+def test_quality_and_quantiser_argument_checks_without_gpu():
+    """The MSSIM, fused-MSSIM and quantiser entry points reject bad arguments on the
+    host, before any launch (documented status codes: 1 argument, 2 shape,
+    8 unsupported)."""
+    plan = rk.rklt_make(8, 0.95)
+    d = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    fm = rk.lib.rklt_fused_mssim
+    assert fm(plan.handle, d, 1, 12, 16, 16, 0, 10, None, None, 0, 0, d, d, d, None) == 2    # H % 8
+    assert fm(plan.handle, d, 1, 16, 16, 8, 0, 10, None, None, 0, 0, d, d, d, None) == 2     # ld < W
+    assert fm(plan.handle, d, 1, 16, 16, 16, 0, 65, None, None, 0, 0, d, d, d, None) == 1    # r > 64
+    assert fm(plan.handle, d, 1, 16, 16, 16, 0, 10, None, None, 0, 0, d, d, None, None) == 1  # no mssim
+    assert fm(plan.handle, d, 0, 16, 16, 16, 0, 10, None, None, 0, 0, d, d, d, None) == 1    # nimg 0
+    assert fm(plan.handle, d, 2, 16, 16, 16, 100, 10, None, None, 0, 0, d, d, d, None) == 2  # image stride
+    assert fm(None, d, 1, 16, 16, 16, 0, 10, None, None, 0, 0, d, d, d, None) == 1          # no plan
+    ms = rk.lib.rklt_mssim
+    assert ms(d, d, 1, 16, 16, 8, 0, 16, 0, d, None) == 2       # ldx < W
+    assert ms(d, d, 1, 16, 16, 16, 0, 16, 0, None, None) == 1   # no output
+    assert ms(d, d, 0, 16, 16, 16, 0, 16, 0, d, None) == 1      # nimg 0
+    q = rk.lib.rklt_fused_quant
+    good = np.full(64, 4.0)
+    bad = good.copy()
+    bad[5] = 0.0
+    assert q(plan.handle, d, 1, 16, 16, 16, 0, 10, bad.ctypes.data, None, None, 0, 0, d, d, None) == 1   # Q <= 0
+    assert q(plan.handle, d, 1, 16, 16, 16, 0, 10, None, None, None, 0, 0, d, d, None) == 1              # no Q
+    assert q(plan.handle, d, 1, 12, 16, 16, 0, 10, good.ctypes.data, None, None, 0, 0, d, d, None) == 2   # H % 8
+    dct = rk.rklt_make_dct(8)
+    assert q(dct.handle, d, 1, 16, 16, 16, 0, 10, good.ctypes.data, None, None, 0, 0, d, d, None) == 8    # real plan
