@@ -103,3 +103,34 @@ def test_quality_and_quantiser_argument_checks_without_gpu():
     assert q(plan.handle, d, 1, 12, 16, 16, 0, 10, good.ctypes.data, None, None, 0, 0, d, d, None) == 2   # H % 8
     dct = rk.rklt_make_dct(8)
     assert q(dct.handle, d, 1, 16, 16, 16, 0, 10, good.ctypes.data, None, None, 0, 0, d, d, None) == 8    # real plan
+
+
+def test_batch_item_checks_without_gpu():
+    """Uneven-batch items are validated on the host before anything is queued: plan
+    index, r, shape, pitch, and the N-byte row alignment the batch kernels read with."""
+    plans8 = [rk.rklt_make(8, 0.95), rk.rklt_make(8, 0.5)]
+    arr8 = rk._plan_array(plans8)
+    d = ctypes.c_void_p(16)
+
+    def item(**kw):
+        it = rk.RklTItem()
+        it.d_img, it.H, it.W, it.ld, it.plan, it.r = 4096, 64, 64, 64, 0, 10
+        it.d_zcoef, it.d_recon, it.ld_recon = None, None, 0
+        for k, v in kw.items():
+            setattr(it, k, v)
+        return (rk.RklTItem * 1)(it)
+
+    def call(items, arr=arr8, nplans=2):
+        return rk.lib.rklt_fused_items(items, 1, ctypes.cast(arr, ctypes.c_void_p), nplans, d, d, None)
+
+    assert call(item(plan=2)) == 1            # plan index out of range
+    assert call(item(r=65)) == 1              # r > 64
+    assert call(item(H=60)) == 2              # H % 8
+    assert call(item(ld=32)) == 2             # ld < W
+    assert call(item(d_img=4100)) == 8        # rows not 8-byte aligned
+    assert call(item(d_img=None)) == 1        # no image
+    assert call(item(d_recon=4096, ld_recon=32)) == 2
+    plans16 = [rk.rklt_make(16, 0.95)]
+    assert call(item(), rk._plan_array(plans16), 1) == 8   # N = 16: not a batch size
+    mixed = [rk.rklt_make(8, 0.95), rk.rklt_make(4, 0.95)]
+    assert call(item(), rk._plan_array(mixed), 2) == 1     # plans of different N
