@@ -536,8 +536,7 @@ rklt_status rklt_server_create(const rklt_plan *const *plans, int nplans, size_t
     s->max_batch = max_batch;
     // two batches in flight per stream: a batch waits for a slot rather than piling
     // launches onto the streams, so under load the requests that arrive meanwhile
-    // join the next batch (at a 4x stress rate the p99 dropped from hundreds of ms to
-    // a few ms against 64 slots)
+    // join the next batch
     s->slots = std::min(64, 2 * nstreams);
     try {
         s->pool.reset(new CopyPool(kCopyWorkers));
