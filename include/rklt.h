@@ -196,11 +196,13 @@ rklt_status rklt_psnr(const uint8_t *d_img, int64_t ld, const float *d_recon, in
  *   d_recon  uint8 reconstruction clip(floor(A' + 1/2), 0, 255), pitch ld_recon bytes;
  *   d_sse    FP64 SSE of the unrounded reconstruction; d_psnr FP32 PSNR (as rklt_psnr).
  * The reconstruction uses A' = T^{-1} (M o C) T^{-T}, which equals That^{-1} B' That^{-T}
- * because the diagonal S cancels (Appendix).  With d_recon NULL and T T^T diagonal
- * (Eq. 1's orthogonal branch; N = 4, 8 on the register path) the SSE is taken by
- * Parseval's identity instead, sum A^2 - sum_retained C_ij^2 / (d_i d_j), in exact
- * integers up to one FP32 rounding per block: the same quantity without the FP32
- * reconstruction error, so it may differ from the call with d_recon in the last bits.
+ * because the diagonal S cancels (Appendix).  When T T^T is diagonal (Eq. 1's
+ * orthogonal branch) and the register path serves the call (N = 4; N = 8 with
+ * r <= 15), the SSE is taken by Parseval's identity, sum A^2 - sum_retained C_ij^2 /
+ * (d_i d_j), in exact integers (one 64-bit sum per tile and per image, divided once
+ * by m^2 = lcm(d)^2), with or without d_recon: the error of the unrounded
+ * reconstruction without FP32 rounding, identical for every subset of the outputs,
+ * and exactly 0 at r = N*N.  Other plans take it from the FP32 reconstruction.
  * Errors: RKLT_ERR_ARG, RKLT_ERR_SHAPE, RKLT_ERR_CUDA. */
 rklt_status rklt_fused(const rklt_plan *plan, const uint8_t *d_img, int H, int W, int64_t ld, int r,
                        float *d_zcoef, uint8_t *d_recon, int64_t ld_recon, double *d_sse,
